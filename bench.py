@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the voxel-grid hot path on GB300.
+
+A step is one measurement of the plain per-frame path: K1 voxelize, K2
+inflate, K3 ray-trace, K4 merge (vg_integrate_depth) and K5 re-centre
+(vg_shift), on the default workload "seq": 640x480 float32 depth frames
+along a seeded trajectory through a 20x20x5 m scene of 200 boxes and
+cylinders, depth 5 m, 10% invalid pixels, depth noise sigma 1% of depth,
+200x200x100 grid at 0.05 m, vox_inf 2, shift every frame.  Inputs are
+synthetic (synth/), all frames resident in HBM before timing.  L2 is
+flushed (a 256 MB write) before every timed step, outside its events.
+
+Prints one JSON line.  value = Mvoxel-updates/s (loc voxels merged per
+frame x frames / summed per-frame device time); per-frame latency p50/p99
+in the same line.  `--impl reference` times the CPU oracle instead (the
+reference arm: the paper's method restated in plain C, single core).
+Under torchrun each rank runs an independent robot (its own seeded
+sequence, no collective on the data path); rank 0 prints.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "per-frame latency p50/p99 and Mvoxel-updates/s, batched/served vs plain, 1 GB300"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="seq")
+    ap.add_argument("--frames", type=int, default=100, help="frames in the synthetic sequence")
+    ap.add_argument("--lanes", type=int, default=0, help="K3 lanes per ray (0 = library default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle sample budget")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (independent robots per rank)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self, gpus):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        if gpus != self.world:
+            raise SystemExit("--gpus %d but WORLD_SIZE %d: launch N>1 with torchrun" % (gpus, self.world))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v):
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([float(v)], device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v):
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([float(v)], device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the run
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sel = [p for t, p in self.samples if t0 <= t <= t1]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[0]) for p in sel if num(p[0]) is not None]
+        mx = [num(p[1]) for p in sel if num(p[1]) is not None]
+        reasons = sorted({self.NAMES[i] for p in sel for i in range(4) if p[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sel)}
+
+
+def visible_gpu_index(local):
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        ids = [c.strip() for c in cvd.split(",") if c.strip()]
+        if local < len(ids):
+            return ids[local]
+    return str(local)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", FALLBACK_HBM_GBS), "measured", d
+    return FALLBACK_HBM_GBS, "fallback", {}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_frames(w, count, budget_s, start=0):
+    """Run the oracle over frames start.. of w (integrate + shift, the same
+    calls as a step) until count frames or budget_s seconds; returns the
+    number of frames and the seconds they took."""
+    from oracle import OracleGrid, OracleParams
+    g = w.grid
+    og = OracleGrid(OracleParams(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf),
+                    w.frames[start % len(w.frames)].robot_pos)
+    done, spent = 0, 0.0
+    while done < count and spent < budget_s:
+        f = w.frames[(start + done) % len(w.frames)]
+        t = time.perf_counter()
+        og.integrate_depth(f.T_wc, f.depth, w.cam.scale)
+        og.shift(f.robot_pos)
+        spent += time.perf_counter() - t
+        done += 1
+    return done, spent
+
+
+def run_reference(args):
+    from synth import make
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = make(args.workload, frames=args.frames)
+    oracle_frames(w, args.warmup, 1e9)
+    n, secs = oracle_frames(w, args.steps, 1e9, start=args.warmup)
+    value = w.nvox * n / secs / 1e6
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mvoxel-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / n * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(w, args),
+        "cpu_baseline": {"value": value, "unit": "Mvoxel-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d frames of the %s sequence, integrate + shift each" % (n, w.name)},
+        "e2e": {"value": value, "unit": "Mvoxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(w, args):
+    return {"workload": "%s: %dx%d %s depth, %d frames, grid %dx%dx%d at %.2f m, vox_inf %d, depth %.1f m, "
+                        "fov %.0fx%.0f, shift every frame" % (
+                            w.name, w.cam.W, w.cam.H, w.cam.dtype, len(w.frames), *w.grid.n, w.grid.vox_size,
+                            w.grid.vox_inf, w.grid.depth, w.cam.fov_x, w.cam.fov_y),
+            "form": "plain (one frame per launch sequence)", "l2": "flushed (256 MB write) before every step",
+            "parallelism": "independent robots per GPU" if args.gpus > 1 else "single GPU"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(kind, w, geom):
+    """Bytes one launch of a kernel must move at minimum."""
+    nvox = w.nvox
+    words = geom["words"]
+    px = w.cam.W * w.cam.H * (2 if w.cam.dtype == "u16" else 4)
+    return {"voxelize": px + 4 * words,      # depth read, occ_raw plane written
+            "inflate": 8 * words,            # occ_raw read, occ_inf written
+            "raytrace": 12 * words,          # occ_inf read, fr and tr written
+            "merge": 2 * nvox + 12 * words,  # loc read+write, three planes read
+            "shift": 2 * nvox}[kind]
+
+
+def run_ours(args):
+    import torch
+    from paper_2112_13169_gb300 import build as vgbuild
+    dist = Dist(args.gpus)
+    torch.cuda.set_device(dist.local)
+    vgbuild.build()
+    from paper_2112_13169_gb300 import vg
+    from synth import make
+
+    seed = None if dist.rank == 0 else 2000 + 17 * dist.rank
+    w = make(args.workload, frames=args.frames, seed=seed)
+    g = w.grid
+    F = len(w.frames)
+    stream = torch.cuda.current_stream()
+    depth_dev = torch.from_numpy(np.stack([f.depth for f in w.frames])).cuda()
+    depth_host = torch.from_numpy(np.stack([f.depth for f in w.frames])).pin_memory()
+    Ts = [f.T_wc for f in w.frames]
+    poss = [f.robot_pos for f in w.frames]
+    scale = w.cam.scale
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out_host = torch.empty(w.nvox, dtype=torch.uint8).pin_memory()
+
+    def new_grid(flags=0):
+        gr = vg.Grid(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, poss[0], flags=flags)
+        if args.lanes:
+            gr.tune(args.lanes)
+        return gr
+
+    def step(gr, k):
+        f = k % F
+        gr.integrate_depth(depth_dev[f], Ts[f], scale)
+        gr.shift(poss[f])
+
+    clocks = ClockSampler(visible_gpu_index(dist.local)) if dist.rank == 0 else None
+
+    # warm-up, then about a second of pre-roll so clocks settle
+    grid = new_grid()
+    for k in range(max(3, args.warmup)):
+        step(grid, k)
+    torch.cuda.synchronize()
+    t_pre = time.time()
+    k = 0
+    while time.time() - t_pre < 1.0:
+        step(grid, k)
+        k += 1
+        if k % 50 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    grid.close()
+
+    # ---- timed region: per-frame device time ------------------------------
+    grid = new_grid()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = grid.profile_read()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step(grid, k)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t_wall1 = time.time()
+    lat_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    launches1 = grid.profile_read()
+    gpu_launches = int(sum(launches1[k][2] - launches0[k][2] for k in vg.KERNELS))
+    grid.close()
+
+    total_s = float(lat_ms.sum()) / 1e3
+    total_s_max = dist.max(total_s)
+    vox_all = dist.sum(w.nvox * args.steps)
+    value = vox_all / total_s_max / 1e6
+
+    # ---- per-kernel profile over the same steps (roofline) ---------------
+    grid = new_grid()
+    grid.profile(True)
+    grid.profile_read(reset=True)
+    for k in range(args.steps):
+        flush.zero_()
+        step(grid, k)
+    torch.cuda.synchronize()
+    prof = grid.profile_read(reset=True)
+    grid.close()
+    # in-grid voxel visits of K3 (stats counters, separate untimed pass)
+    grid = new_grid(vg.VG_FLAG_STATS)
+    for k in range(args.steps):
+        step(grid, k)
+    st = grid.stats()
+    grid.close()
+
+    # ---- end to end: host buffers through the C ABI -----------------------
+    grid = new_grid()
+    e2e_s = 0.0
+    for k in range(args.steps):
+        f = k % F
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        grid.integrate_depth(depth_host[f], Ts[f], scale)     # H2D inside the library
+        grid.shift(poss[f])
+        grid.read(out_host)                                   # D2H of the grid
+        stream.synchronize()
+        e2e_s += time.perf_counter() - t
+    grid.close()
+    e2e_value = dist.sum(w.nvox * args.steps) / dist.max(e2e_s) / 1e6
+
+    if clocks:
+        clocks.stop()
+
+    if dist.rank != 0:
+        dist.close()
+        return 0
+
+    hbm_peak, peak_kind, peaks = measured_peaks()
+    geom = {"words": ((g.n[0] + 31) // 32 + 3) // 4 * 4 * g.n[1] * g.n[2]}
+    kern = {}
+    for name in vg.KERNELS:
+        ms, timed, total = prof[name]
+        if timed:
+            avg_s = ms / timed / 1e3
+            kern[name] = {"avg_us": avg_s * 1e6, "launches": timed, "share": 0.0,
+                          "alg_bytes": algorithmic_bytes(name, w, geom),
+                          "gbs": algorithmic_bytes(name, w, geom) / avg_s / 1e9}
+    tot = sum(v["avg_us"] * v["launches"] for v in kern.values())
+    for v in kern.values():
+        v["share"] = v["avg_us"] * v["launches"] / tot
+    dom = max(kern, key=lambda k: kern[k]["avg_us"] * kern[k]["launches"])
+    d = kern[dom]
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": d["gbs"] / hbm_peak, "traffic": None, "peak_source": peak_kind,
+                "alg_bytes_per_launch": d["alg_bytes"], "avg_us": d["avg_us"]}
+    visits_per_frame = st["ray_visits"] / max(1, st["frames"])
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        n, secs = oracle_frames(w, F, args.cpu_seconds)
+        cpu = {"value": w.nvox * n / secs / 1e6, "unit": "Mvoxel-updates/s", "cores": 1, "kind": "oracle",
+               "sample": "first %d frames of the %s sequence, integrate + shift each, single thread" % (n, w.name)}
+
+    summ = clocks.summary(t_pre - 0.5, t_wall1 + 0.5) if clocks else {"sm_mhz": None, "sm_max_mhz": None,
+                                                                       "reasons": [], "samples": 0}
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mvoxel-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(lat_ms.mean()),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(w, args),
+        "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                       "mean": float(lat_ms.mean()), "max": float(lat_ms.max())},
+        "e2e": {"value": e2e_value, "unit": "Mvoxel-updates/s",
+                "h2d_bytes_per_step": int(depth_host[0].numel() * depth_host.element_size()),
+                "d2h_bytes_per_step": int(w.nvox),
+                "ms_per_step": e2e_s / args.steps * 1e3},
+        "gpu_launches": gpu_launches,
+        "roofline": roofline,
+        "kernels": {k: {"avg_us": round(v["avg_us"], 3), "share": round(v["share"], 4),
+                        "alg_GBps": round(v["gbs"], 1)} for k, v in kern.items()},
+        "ray_visits_per_frame": visits_per_frame,
+        "cpu_baseline": cpu,
+        "clocks": {"sm_mhz": summ["sm_mhz"], "sm_max_mhz": summ["sm_max_mhz"], "reasons": summ["reasons"],
+                   "samples": summ["samples"]},
+        "wall_s_timed_region": t_wall1 - t_wall0,
+    }
+    print(json.dumps(line))
+    dist.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,232 @@
+/*
+ * vg.h -- C ABI of the GB300 voxel-grid library (libvg.so).
+ *
+ * Implements the method of "GPU Accelerated Voxel Grid Generation for fast
+ * MAV Exploration" (Toumieh & Lambert, arXiv 2112.13169): every depth image
+ * or dense point cloud becomes a robot-centred local grid of occupied, free
+ * and unknown voxels.  Each step runs in a hand-written sm_103a kernel:
+ *   K1 transform + voxelize     (Sec. IV-B, Alg. 1, first half)
+ *   K2 inflate by vox_inf       (Sec. IV-B, Alg. 1, the three nested loops)
+ *   K3 free-space ray-trace     (Sec. IV-C, Alg. 2)
+ *   K4 merge into loc_grid      (Sec. IV-D, Alg. 3)
+ *   K5 shift (re-centre)        (Sec. IV-E)
+ * There is no CPU fallback: every call either enqueues device work or fails.
+ *
+ * Conventions shared by all entry points
+ *  - Grid layout (Sec. IV-D): one byte per voxel, idx = x + y*Nx + z*Nx*Ny.
+ *    Voxel codes: VG_UNK 0, VG_FREE 1, VG_OCC 2, VG_TRACED 3
+ *    ("unknown and traced", Sec. IV-C).  The paper names the states but gives
+ *    no numeric codes; these are this library's.
+ *  - Frames: the camera optical frame is x right, y down, z forward; a depth
+ *    image holds z-depth.  The world and the grid are ENU-aligned (Sec. IV-A).
+ *  - T_wc: row-major 4x4 double, camera optical frame -> world (T^w_c of
+ *    Table I).  The library composes T^v_c = T^v_w T^w_c on the host in
+ *    double and rounds it to float once (Sec. IV-B).
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Calls are asynchronous with respect to the host unless stated; inputs
+ *    must stay valid until the enqueued work completes.  Calls on one grid
+ *    must be issued from one host thread at a time; work on different grids
+ *    may overlap freely.
+ *  - Errors: every call returns a status (VG_OK = 0).  Device faults are
+ *    asynchronous and surface as VG_ECUDA at a later call.  No call throws,
+ *    prints, or exits.
+ *  - Numerics: FP32, IEEE round-to-nearest per operation, no FMA
+ *    contraction, in the order the oracle states; grids are bit-exact
+ *    against the CPU oracle.
+ */
+#ifndef VG_H
+#define VG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VG_API __attribute__((visibility("default")))
+#else
+#define VG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    VG_OK = 0,
+    VG_EINVAL = 1,   /* bad argument: NULL pointer, bad size, non-finite pose ... */
+    VG_ENOMEM = 2,   /* device or host allocation failed */
+    VG_ECUDA = 3,    /* a CUDA call failed (including an earlier asynchronous fault) */
+    VG_ETIMEOUT = 4, /* a bounded device wait ran out */
+    VG_EBUSY = 5     /* resource in use */
+};
+
+/* Voxel states stored in loc_grid. */
+enum { VG_UNK = 0, VG_FREE = 1, VG_OCC = 2, VG_TRACED = 3 };
+
+/* Depth pixel types. */
+enum { VG_DEPTH_F32 = 0, VG_DEPTH_U16 = 1 };
+
+/* Where a buffer lives. */
+enum { VG_MEM_DEVICE = 0, VG_MEM_HOST = 1 };
+
+/* Grid flags. */
+enum {
+    VG_FLAG_STATS = 1u << 0   /* count in-grid points and ray-voxel visits (vg_stats) */
+};
+
+/*
+ * Table I parameters of one local grid.
+ *  grid_size  voxels per axis (x, y, z), each >= 1, total < 2^31.  The paper
+ *             gives sizes in metres (Sec. V); callers convert with
+ *             round(m / vox_size).
+ *  vox_size   voxel edge in metres, finite, > 0.
+ *  fov_x_deg, fov_y_deg
+ *             camera field of view in degrees, in (0, 180).
+ *  depth      range in metres to clear by ray-tracing (Sec. IV-C) and the
+ *             largest depth accepted from a depth image; finite, > 0.
+ *  vox_inf    inflation radius in voxels (Sec. IV-B), 0 <= vox_inf <= 15.
+ *  flags      VG_FLAG_* bits.
+ */
+typedef struct {
+    int32_t grid_size[3];
+    float vox_size;
+    float fov_x_deg;
+    float fov_y_deg;
+    float depth;
+    int32_t vox_inf;
+    uint32_t flags;
+} vg_params;
+
+typedef struct vg_grid vg_grid;
+
+/* Counters accumulated since creation when VG_FLAG_STATS is set. */
+typedef struct {
+    uint64_t frames;          /* vg_integrate_* calls */
+    uint64_t points_in_grid;  /* valid points that landed inside the grid (K1) */
+    uint64_t ray_visits;      /* in-grid voxel visits over all rays (K3) */
+} vg_stats_t;
+
+/*
+ * Voxel grid set-up (Sec. IV-A).  Allocates loc_grid and the measurement
+ * planes on the current device (one allocation, owned by the grid) and sets
+ * every voxel to VG_UNK.  The origin is placed so that the robot at
+ * robot_pos_w (world metres) sits in voxel floor(N/2) of every axis:
+ * origin_k = floor(p_k / vox_size) - floor(N_k / 2), computed in double.
+ * Synchronises `stream` once before returning.
+ * Errors: VG_EINVAL (NULL, out-of-range parameter), VG_ENOMEM, VG_ECUDA.
+ */
+VG_API int vg_create(const vg_params *params, const double robot_pos_w[3], void *stream,
+              vg_grid **out);
+
+/* Frees the grid (synchronises the device first).  NULL is accepted. */
+VG_API void vg_destroy(vg_grid *grid);
+
+/*
+ * One measurement from a depth image (Sec. IV, steps 2-4): K1 voxelizes the
+ * valid pixels, K2 inflates, K3 traces the ray bundle of Sec. IV-C, K4
+ * merges the measurement into loc_grid (Alg. 3).
+ *  depth        W x H pixels, row-major, tightly packed.  dtype VG_DEPTH_F32
+ *               (metres) or VG_DEPTH_U16 (metres = raw * depth_scale).
+ *  mem          VG_MEM_DEVICE: depth is a device pointer, read in place.
+ *               VG_MEM_HOST: depth is host memory; it is copied with
+ *               cudaMemcpyAsync into a staging buffer the grid owns (grown
+ *               on first use of a larger frame; pinned host memory makes the
+ *               copy asynchronous).
+ *  depth_scale  used for VG_DEPTH_U16 only; finite, > 0.
+ *  T_wc         camera pose, see above; must be finite.
+ * A pixel is valid iff its depth d is finite, > 0 and <= params.depth.  The
+ * pinhole model takes fx = (W/2)/tan(fov_x/2), cx = (W-1)/2 (y likewise).
+ * Errors: VG_EINVAL, VG_ENOMEM (staging), VG_ECUDA.
+ */
+VG_API int vg_integrate_depth(vg_grid *grid, const void *depth, int32_t mem, int32_t width,
+                       int32_t height, int32_t dtype, float depth_scale,
+                       const double T_wc[16], void *stream);
+
+/*
+ * One measurement from a dense point cloud (Sec. IV): n points, xyz float
+ * triples in the camera optical frame, packed.  A point is valid iff its
+ * three coordinates are finite (no range filter).  mem as above.
+ * Errors: VG_EINVAL, VG_ENOMEM (staging), VG_ECUDA.
+ */
+VG_API int vg_integrate_points(vg_grid *grid, const float *xyz, int32_t mem, int64_t n,
+                        const double T_wc[16], void *stream);
+
+/*
+ * Re-centre the grid on the robot (Sec. IV-E): the new origin o' is computed
+ * as in vg_create; with delta = o' - o, loc'[i] = loc[i + delta] where that
+ * voxel exists, else VG_UNK.  No device work when delta is zero.
+ * Errors: VG_EINVAL, VG_ECUDA.
+ */
+VG_API int vg_shift(vg_grid *grid, const double robot_pos_w[3], void *stream);
+
+/*
+ * Copy loc_grid (Nx*Ny*Nz bytes, layout above) to dst, enqueued on stream;
+ * dst is valid once that work completes.  dst_mem is VG_MEM_DEVICE or
+ * VG_MEM_HOST; dst_bytes must be >= Nx*Ny*Nz.  origin (may be NULL)
+ * receives the grid origin (voxel index of voxel (0,0,0) in the world
+ * lattice) as of this call.
+ * Errors: VG_EINVAL, VG_ECUDA.
+ */
+VG_API int vg_read(vg_grid *grid, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes,
+            int32_t origin[3], void *stream);
+
+/*
+ * Restore loc_grid and its origin (checkpoint / resume): src holds
+ * Nx*Ny*Nz bytes of voxel codes 0..3 (not checked), src_bytes must equal
+ * Nx*Ny*Nz.  Errors: VG_EINVAL, VG_ECUDA.
+ */
+VG_API int vg_write(vg_grid *grid, const uint8_t *src, int32_t src_mem, int64_t src_bytes,
+             const int32_t origin[3], void *stream);
+
+/* Current origin (host-side state; no device work). */
+VG_API int vg_get_origin(const vg_grid *grid, int32_t origin[3]);
+
+/* Device bytes one grid with these parameters holds (0 if invalid). */
+VG_API int64_t vg_grid_bytes(const vg_params *params);
+
+/* Ray bundle of Sec. IV-C: out = {vox_depth, hw, hh}; vox_width = 2hw+1,
+ * vox_height = 2hh+1; returns the ray count (0 if invalid). */
+VG_API int64_t vg_ray_bundle(const vg_params *params, int32_t out[3]);
+
+/* Counters (VG_FLAG_STATS); synchronises the device. */
+VG_API int vg_stats(vg_grid *grid, vg_stats_t *out);
+
+/* Kernels of one measurement, for profiling and launch counts. */
+enum {
+    VG_K_VOXELIZE = 0, /* K1 */
+    VG_K_INFLATE = 1,  /* K2 */
+    VG_K_RAYTRACE = 2, /* K3 */
+    VG_K_MERGE = 3,    /* K4 */
+    VG_K_SHIFT = 4,    /* K5 */
+    VG_NKERNELS = 5
+};
+
+/*
+ * Per-kernel timing.  While enabled, every kernel launch of this grid is
+ * bracketed by two CUDA events recorded on the launch's own stream (up to
+ * 65536 launches are kept; later ones are counted but not timed).
+ * vg_profile_read synchronises the device, writes the summed event time in
+ * milliseconds and the number of timed launches per kernel, and (if reset)
+ * forgets them.  launches_total (may be NULL) receives the number of kernel
+ * launches this grid has issued since creation, timed or not.
+ * Errors: VG_EINVAL, VG_ENOMEM (event pool), VG_ECUDA.
+ */
+VG_API int vg_profile_enable(vg_grid *grid, int32_t enable);
+VG_API int vg_profile_read(vg_grid *grid, double ms[VG_NKERNELS], int64_t timed[VG_NKERNELS],
+                           int64_t launches_total[VG_NKERNELS], int32_t reset);
+
+/*
+ * Tuning knobs (defaults are set by vg_create):
+ *  VG_TUNE_RT_LANES  lanes of a warp that share one ray in K3: 1, 2, 4, 8,
+ *                    16 or 32 (default 8).  Results do not depend on it.
+ * Errors: VG_EINVAL.
+ */
+enum { VG_TUNE_RT_LANES = 0 };
+VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
+
+/* Static description of a status code. */
+VG_API const char *vg_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

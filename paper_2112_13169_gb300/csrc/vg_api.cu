@@ -1,0 +1,497 @@
+// vg_api.cu -- host side of the C ABI declared in include/vg.h.
+//
+// Per-frame host work is argument checking and the set-up arithmetic the
+// paper assigns to the CPU (Sec. IV-B: T^v_c = T^v_w T^w_c is composed on the
+// host and passed to the kernels), plus the pinhole intrinsics and the ray
+// bundle size, all in double and rounded once to float / integer:
+//   origin_k   = floor(p_k / vox_size) - floor(N_k / 2)          (Sec. IV-A)
+//   R^v_c      = R^w_c,  t^v_c = t^w_c - origin * vox_size       (Sec. IV-B)
+//   vox_depth  = lround(depth / vox_size)                         (Sec. IV-C)
+//   hw         = lround(tan(fov_x / 2) * vox_depth), hh likewise
+//   fx         = (W / 2) / tan(fov_x / 2), cx = (W - 1) / 2, y likewise
+// with fov/2 in radians taken as fov_deg * pi / 360.  Everything else runs
+// in the kernels K1..K5, enqueued on the caller's stream without host sync.
+#include "vg.h"
+#include "vg_internal.cuh"
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+using vg::FrameArgs;
+using vg::PlaneGeom;
+
+struct vg_grid {
+    vg_params p;
+    PlaneGeom g;
+    int32_t origin[3];
+    int32_t vd, hw, hh;
+    int lanes_per_ray;
+    int device;
+    uint8_t *base;        // the one device allocation
+    uint8_t *loc;
+    uint8_t *loc_alt;
+    vg::Planes pl;
+    unsigned long long *stats;
+    void *staging;        // device copy of host inputs
+    size_t staging_bytes;
+    uint64_t frames;
+    int64_t launches[VG_NKERNELS];
+    // profiling: event pairs recorded around launches
+    bool prof_on;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+    size_t prof_used;
+};
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+int status_of(cudaError_t e) {
+    if (e == cudaSuccess) return VG_OK;
+    if (e == cudaErrorMemoryAllocation) return VG_ENOMEM;
+    return VG_ECUDA;
+}
+
+double half_fov(float deg) { return (double)deg * kPi / 360.0; }
+
+bool finite3(const double v[3]) {
+    return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+bool params_ok(const vg_params *p) {
+    if (!p) return false;
+    int64_t nv = 1;
+    for (int k = 0; k < 3; ++k) {
+        if (p->grid_size[k] < 1) return false;
+        nv *= p->grid_size[k];
+        if (nv >= (int64_t(1) << 31)) return false;
+    }
+    if (!(std::isfinite(p->vox_size) && p->vox_size > 0.0f)) return false;
+    if (!(p->fov_x_deg > 0.0f && p->fov_x_deg < 180.0f)) return false;
+    if (!(p->fov_y_deg > 0.0f && p->fov_y_deg < 180.0f)) return false;
+    if (!(std::isfinite(p->depth) && p->depth > 0.0f)) return false;
+    if (p->vox_inf < 0 || p->vox_inf > vg::kMaxInflate) return false;
+    const double vd = (double)p->depth / (double)p->vox_size;
+    if (!(vd < 1.0e6)) return false;
+    return true;
+}
+
+PlaneGeom geom_of(const vg_params *p) {
+    PlaneGeom g;
+    g.nx = p->grid_size[0];
+    g.ny = p->grid_size[1];
+    g.nz = p->grid_size[2];
+    const int32_t w = (g.nx + 31) / 32;
+    g.wx = (w + 3) / 4 * 4;
+    g.words = (int64_t)g.wx * g.ny * g.nz;
+    g.nvox = (int64_t)g.nx * g.ny * g.nz;
+    return g;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t loc, loc_alt, occ_raw, occ_inf, fr, tr, stats, total;
+};
+
+Layout layout_of(const PlaneGeom &g) {
+    Layout L;
+    size_t off = 0;
+    const size_t locb = align256((size_t)g.nvox), planeb = align256((size_t)g.words * 4);
+    L.loc = off; off += locb;
+    L.loc_alt = off; off += locb;
+    L.occ_raw = off; off += planeb;
+    L.occ_inf = off; off += planeb;
+    L.fr = off; off += planeb;
+    L.tr = off; off += planeb;
+    L.stats = off; off += 256;
+    L.total = off;
+    return L;
+}
+
+void bundle_of(const vg_params *p, int32_t &vd, int32_t &hw, int32_t &hh) {
+    const long d = lround((double)p->depth / (double)p->vox_size);
+    vd = (int32_t)d;
+    hw = (int32_t)lround(tan(half_fov(p->fov_x_deg)) * (double)d);
+    hh = (int32_t)lround(tan(half_fov(p->fov_y_deg)) * (double)d);
+}
+
+void origin_of(const vg_params *p, const double pos[3], int32_t o[3]) {
+    for (int k = 0; k < 3; ++k)
+        o[k] = (int32_t)floor(pos[k] / (double)p->vox_size) - p->grid_size[k] / 2;
+}
+
+bool pose_of(const vg_grid *G, const double T_wc[16], vg::Pose32 &T) {
+    if (!T_wc) return false;
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(T_wc[i])) return false;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) T.R[r * 3 + c] = (float)T_wc[r * 4 + c];
+        T.t[r] = (float)(T_wc[r * 4 + 3] - (double)G->origin[r] * (double)G->p.vox_size);
+    }
+    return true;
+}
+
+// Keeps the caller's current device and switches to the grid's for the call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+std::once_flag g_configured[64];
+cudaError_t g_config_err[64];
+
+cudaError_t configure_device(int dev) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::call_once(g_configured[dev], [dev] { g_config_err[dev] = vg::configure_inflate(); });
+    return g_config_err[dev];
+}
+
+int stage_input(vg_grid *G, const void *src, size_t bytes, cudaStream_t s, const void **dev_ptr) {
+    if (bytes > G->staging_bytes) {
+        // grow-only staging buffer; the old one may still be read by queued work
+        if (G->staging) {
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return status_of(e);
+            cudaFree(G->staging);
+            G->staging = nullptr;
+            G->staging_bytes = 0;
+        }
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? VG_ENOMEM : VG_ECUDA;
+        G->staging = p;
+        G->staging_bytes = bytes;
+    }
+    cudaError_t e = cudaMemcpyAsync(G->staging, src, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return status_of(e);
+    *dev_ptr = G->staging;
+    return VG_OK;
+}
+
+FrameArgs frame_args(vg_grid *G, const vg::Pose32 &T) {
+    FrameArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = G->g;
+    a.T = T;
+    a.vs = G->p.vox_size;
+    a.depth_max = G->p.depth;
+    a.vd = G->vd;
+    a.hw = G->hw;
+    a.hh = G->hh;
+    a.r = G->p.vox_inf;
+    a.pl = G->pl;
+    a.loc = G->loc;
+    a.stats = (G->p.flags & VG_FLAG_STATS) ? G->stats : nullptr;
+    return a;
+}
+
+constexpr size_t kProfPairs = 65536;
+
+// Runs one kernel launcher, counting it and, when profiling, bracketing it
+// with events on its stream.
+template <typename F>
+cudaError_t launch(vg_grid *G, int kind, cudaStream_t s, F &&fn) {
+    ++G->launches[kind];
+    if (!G->prof_on || G->prof_used >= kProfPairs) return fn();
+    const size_t i = G->prof_used++;
+    cudaError_t e = cudaEventRecord(G->prof_ev[2 * i], s);
+    if (e != cudaSuccess) return e;
+    e = fn();
+    if (e != cudaSuccess) return e;
+    G->prof_kind[i] = kind;
+    return cudaEventRecord(G->prof_ev[2 * i + 1], s);
+}
+
+// K2..K4 after K1 has filled occ_raw.
+cudaError_t finish_frame(vg_grid *G, FrameArgs &a, cudaStream_t s) {
+    cudaError_t e;
+    if (a.r > 0) {
+        e = launch(G, VG_K_INFLATE, s, [&] { return vg::launch_inflate(a, s); });
+        if (e != cudaSuccess) return e;
+    } else {
+        a.pl.occ_inf = a.pl.occ_raw;   // no inflation: the raw plane is the inflated one
+    }
+    e = launch(G, VG_K_RAYTRACE, s, [&] { return vg::launch_raytrace(a, G->lanes_per_ray, s); });
+    if (e != cudaSuccess) return e;
+    return launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge(a, s); });
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vg_strerror(int status) {
+    switch (status) {
+    case VG_OK: return "ok";
+    case VG_EINVAL: return "invalid argument";
+    case VG_ENOMEM: return "out of memory";
+    case VG_ECUDA: return "CUDA error";
+    case VG_ETIMEOUT: return "device wait timed out";
+    case VG_EBUSY: return "busy";
+    default: return "unknown status";
+    }
+}
+
+int64_t vg_grid_bytes(const vg_params *params) {
+    if (!params_ok(params)) return 0;
+    return (int64_t)layout_of(geom_of(params)).total;
+}
+
+int64_t vg_ray_bundle(const vg_params *params, int32_t out[3]) {
+    if (!params_ok(params) || !out) return 0;
+    bundle_of(params, out[0], out[1], out[2]);
+    return (2 * (int64_t)out[1] + 1) * (2 * (int64_t)out[2] + 1);
+}
+
+int vg_create(const vg_params *params, const double robot_pos_w[3], void *stream, vg_grid **out) {
+    if (!out) return VG_EINVAL;
+    *out = nullptr;
+    if (!params_ok(params) || !robot_pos_w || !finite3(robot_pos_w)) return VG_EINVAL;
+    vg_grid *G = new (std::nothrow) vg_grid();
+    if (!G) return VG_ENOMEM;
+    G->p = *params;
+    G->g = geom_of(params);
+    origin_of(params, robot_pos_w, G->origin);
+    bundle_of(params, G->vd, G->hw, G->hh);
+    G->lanes_per_ray = 8;
+    cudaError_t e = cudaGetDevice(&G->device);
+    if (e == cudaSuccess) e = configure_device(G->device);
+    const Layout L = layout_of(G->g);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&G->base, L.total);
+    if (e != cudaSuccess) {
+        delete G;
+        return status_of(e);
+    }
+    G->loc = G->base + L.loc;
+    G->loc_alt = G->base + L.loc_alt;
+    G->pl.occ_raw = reinterpret_cast<uint32_t *>(G->base + L.occ_raw);
+    G->pl.occ_inf = reinterpret_cast<uint32_t *>(G->base + L.occ_inf);
+    G->pl.fr = reinterpret_cast<uint32_t *>(G->base + L.fr);
+    G->pl.tr = reinterpret_cast<uint32_t *>(G->base + L.tr);
+    G->stats = reinterpret_cast<unsigned long long *>(G->base + L.stats);
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemsetAsync(G->base, 0, L.total, s);   // VG_UNK == 0, planes empty
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaFree(G->base);
+        delete G;
+        return status_of(e);
+    }
+    *out = G;
+    return VG_OK;
+}
+
+void vg_destroy(vg_grid *G) {
+    if (!G) return;
+    DeviceGuard dg(G->device);
+    cudaDeviceSynchronize();
+    for (cudaEvent_t ev : G->prof_ev) cudaEventDestroy(ev);
+    cudaFree(G->staging);
+    cudaFree(G->base);
+    delete G;
+}
+
+int vg_profile_enable(vg_grid *G, int32_t enable) {
+    if (!G) return VG_EINVAL;
+    DeviceGuard dg(G->device);
+    if (!dg.ok) return VG_ECUDA;
+    if (enable && G->prof_ev.empty()) {
+        try {
+            G->prof_ev.resize(2 * kProfPairs, nullptr);
+            G->prof_kind.resize(kProfPairs, 0);
+        } catch (...) {
+            G->prof_ev.clear();
+            return VG_ENOMEM;
+        }
+        for (auto &ev : G->prof_ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return status_of(e);
+        }
+    }
+    G->prof_on = enable != 0;
+    return VG_OK;
+}
+
+int vg_profile_read(vg_grid *G, double ms[VG_NKERNELS], int64_t timed[VG_NKERNELS],
+                    int64_t launches_total[VG_NKERNELS], int32_t reset) {
+    if (!G) return VG_EINVAL;
+    DeviceGuard dg(G->device);
+    if (!dg.ok) return VG_ECUDA;
+    double acc[VG_NKERNELS] = {0, 0, 0, 0, 0};
+    int64_t cnt[VG_NKERNELS] = {0, 0, 0, 0, 0};
+    if (G->prof_used) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return status_of(e);
+        for (size_t i = 0; i < G->prof_used; ++i) {
+            float t = 0.0f;
+            e = cudaEventElapsedTime(&t, G->prof_ev[2 * i], G->prof_ev[2 * i + 1]);
+            if (e != cudaSuccess) return status_of(e);
+            acc[G->prof_kind[i]] += t;
+            cnt[G->prof_kind[i]] += 1;
+        }
+    }
+    for (int k = 0; k < VG_NKERNELS; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (timed) timed[k] = cnt[k];
+        if (launches_total) launches_total[k] = G->launches[k];
+    }
+    if (reset) G->prof_used = 0;
+    return VG_OK;
+}
+
+int vg_tune(vg_grid *G, int32_t knob, int32_t value) {
+    if (!G) return VG_EINVAL;
+    if (knob == VG_TUNE_RT_LANES) {
+        if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
+            return VG_EINVAL;
+        G->lanes_per_ray = value;
+        return VG_OK;
+    }
+    return VG_EINVAL;
+}
+
+int vg_integrate_depth(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32_t height,
+                       int32_t dtype, float depth_scale, const double T_wc[16], void *stream) {
+    if (!G || !depth || width < 1 || height < 1) return VG_EINVAL;
+    if ((int64_t)width * height >= (int64_t(1) << 31)) return VG_EINVAL;
+    if (dtype != VG_DEPTH_F32 && dtype != VG_DEPTH_U16) return VG_EINVAL;
+    if (mem != VG_MEM_DEVICE && mem != VG_MEM_HOST) return VG_EINVAL;
+    if (dtype == VG_DEPTH_U16 && !(std::isfinite(depth_scale) && depth_scale > 0.0f)) return VG_EINVAL;
+    vg::Pose32 T;
+    if (!pose_of(G, T_wc, T)) return VG_EINVAL;
+    DeviceGuard dg(G->device);
+    if (!dg.ok) return VG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *dptr = depth;
+    if (mem == VG_MEM_HOST) {
+        const size_t bytes = (size_t)width * height * (dtype == VG_DEPTH_F32 ? 4 : 2);
+        int rc = stage_input(G, depth, bytes, s, &dptr);
+        if (rc != VG_OK) return rc;
+    }
+    FrameArgs a = frame_args(G, T);
+    a.depth = dptr;
+    a.W = width;
+    a.H = height;
+    a.scale = (dtype == VG_DEPTH_U16) ? depth_scale : 1.0f;
+    a.fx = (float)(((double)width / 2.0) / tan(half_fov(G->p.fov_x_deg)));
+    a.fy = (float)(((double)height / 2.0) / tan(half_fov(G->p.fov_y_deg)));
+    a.cx = (float)(((double)width - 1.0) / 2.0);
+    a.cy = (float)(((double)height - 1.0) / 2.0);
+    cudaError_t e = launch(G, VG_K_VOXELIZE, s, [&] { return vg::launch_voxelize_depth(a, dtype, s); });
+    if (e == cudaSuccess) e = finish_frame(G, a, s);
+    if (e != cudaSuccess) return status_of(e);
+    ++G->frames;
+    return VG_OK;
+}
+
+int vg_integrate_points(vg_grid *G, const float *xyz, int32_t mem, int64_t n, const double T_wc[16],
+                        void *stream) {
+    if (!G || n < 0 || (n > 0 && !xyz) || n >= (int64_t(1) << 31)) return VG_EINVAL;
+    if (mem != VG_MEM_DEVICE && mem != VG_MEM_HOST) return VG_EINVAL;
+    vg::Pose32 T;
+    if (!pose_of(G, T_wc, T)) return VG_EINVAL;
+    DeviceGuard dg(G->device);
+    if (!dg.ok) return VG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const void *dptr = xyz;
+    if (mem == VG_MEM_HOST && n > 0) {
+        int rc = stage_input(G, xyz, (size_t)n * 12, s, &dptr);
+        if (rc != VG_OK) return rc;
+    }
+    FrameArgs a = frame_args(G, T);
+    a.xyz = static_cast<const float *>(dptr);
+    a.npts = n;
+    cudaError_t e = launch(G, VG_K_VOXELIZE, s, [&] { return vg::launch_voxelize_points(a, s); });
+    if (e == cudaSuccess) e = finish_frame(G, a, s);
+    if (e != cudaSuccess) return status_of(e);
+    ++G->frames;
+    return VG_OK;
+}
+
+int vg_shift(vg_grid *G, const double robot_pos_w[3], void *stream) {
+    if (!G || !robot_pos_w || !finite3(robot_pos_w)) return VG_EINVAL;
+    int32_t o2[3];
+    origin_of(&G->p, robot_pos_w, o2);
+    const int32_t delta[3] = {o2[0] - G->origin[0], o2[1] - G->origin[1], o2[2] - G->origin[2]};
+    if (delta[0] == 0 && delta[1] == 0 && delta[2] == 0) return VG_OK;
+    DeviceGuard dg(G->device);
+    if (!dg.ok) return VG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (std::abs((int64_t)delta[0]) >= G->g.nx || std::abs((int64_t)delta[1]) >= G->g.ny ||
+        std::abs((int64_t)delta[2]) >= G->g.nz) {
+        e = cudaMemsetAsync(G->loc, 0, (size_t)G->g.nvox, s);   // nothing survives
+    } else {
+        e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, delta, G->loc, G->loc_alt, s); });
+        if (e == cudaSuccess) {
+            uint8_t *t = G->loc;
+            G->loc = G->loc_alt;
+            G->loc_alt = t;
+        }
+    }
+    if (e != cudaSuccess) return status_of(e);
+    std::memcpy(G->origin, o2, sizeof(o2));
+    return VG_OK;
+}
+
+int vg_read(vg_grid *G, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes, int32_t origin[3],
+            void *stream) {
+    if (!G || !dst || dst_bytes < G->g.nvox) return VG_EINVAL;
+    if (dst_mem != VG_MEM_DEVICE && dst_mem != VG_MEM_HOST) return VG_EINVAL;
+    DeviceGuard dg(G->device);
+    if (!dg.ok) return VG_ECUDA;
+    const cudaMemcpyKind kind = dst_mem == VG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpyAsync(dst, G->loc, (size_t)G->g.nvox, kind, (cudaStream_t)stream);
+    if (e != cudaSuccess) return status_of(e);
+    if (origin) std::memcpy(origin, G->origin, sizeof(G->origin));
+    return VG_OK;
+}
+
+int vg_write(vg_grid *G, const uint8_t *src, int32_t src_mem, int64_t src_bytes, const int32_t origin[3],
+             void *stream) {
+    if (!G || !src || !origin || src_bytes != G->g.nvox) return VG_EINVAL;
+    if (src_mem != VG_MEM_DEVICE && src_mem != VG_MEM_HOST) return VG_EINVAL;
+    DeviceGuard dg(G->device);
+    if (!dg.ok) return VG_ECUDA;
+    const cudaMemcpyKind kind = src_mem == VG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaMemcpyAsync(G->loc, src, (size_t)G->g.nvox, kind, (cudaStream_t)stream);
+    if (e != cudaSuccess) return status_of(e);
+    std::memcpy(G->origin, origin, sizeof(G->origin));
+    return VG_OK;
+}
+
+int vg_get_origin(const vg_grid *G, int32_t origin[3]) {
+    if (!G || !origin) return VG_EINVAL;
+    std::memcpy(origin, G->origin, sizeof(G->origin));
+    return VG_OK;
+}
+
+int vg_stats(vg_grid *G, vg_stats_t *out) {
+    if (!G || !out) return VG_EINVAL;
+    DeviceGuard dg(G->device);
+    if (!dg.ok) return VG_ECUDA;
+    unsigned long long h[3] = {0, 0, 0};
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h, G->stats, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return status_of(e);
+    out->frames = G->frames;
+    out->points_in_grid = h[1];
+    out->ray_visits = h[2];
+    return VG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// vg_internal.cuh -- types shared by the kernels and the host library.
+//
+// Device data layout of one grid (one cudaMalloc, carved in this order):
+//   loc      Nx*Ny*Nz bytes, the paper's index order idx = x + y*Nx + z*Nx*Ny
+//   loc_alt  the same size; target of the out-of-place shift (ping-pong)
+//   occ_raw, occ_inf, fr, tr
+//            bit planes of the measurement grid.  Bit b of word
+//            (z*Ny + y)*WX + w is voxel x = 32*w + b of row (y, z).  WX is
+//            ceil(Nx/32) rounded up to a multiple of 4 words so every row
+//            starts on a 16-byte boundary.  Bits with x >= Nx stay 0.
+//   stats    three u64 counters (VG_FLAG_STATS)
+// The planes are all-zero between frames: K4 clears every word it reads.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vg {
+
+constexpr int kMaxInflate = 15;
+
+struct PlaneGeom {
+    int32_t nx, ny, nz;
+    int32_t wx;        // words per row
+    int64_t words;     // wx * ny * nz
+    int64_t nvox;      // nx * ny * nz
+};
+
+// T^v_c rounded to float: R row-major, t in metres.
+struct Pose32 {
+    float R[9];
+    float t[3];
+};
+
+struct Planes {
+    uint32_t *occ_raw;
+    uint32_t *occ_inf;
+    uint32_t *fr;
+    uint32_t *tr;
+};
+
+struct FrameArgs {
+    PlaneGeom g;
+    Pose32 T;
+    float vs;          // vox_size
+    float depth_max;   // params.depth
+    // depth image input
+    const void *depth;
+    int32_t W, H;
+    float scale;       // u16 -> metres
+    float fx, fy, cx, cy;
+    // point cloud input
+    const float *xyz;
+    int64_t npts;
+    // ray bundle
+    int32_t vd, hw, hh;
+    int32_t r;         // vox_inf
+    Planes pl;
+    uint8_t *loc;
+    unsigned long long *stats;  // NULL unless VG_FLAG_STATS
+};
+
+inline __host__ __device__ int64_t plane_word(const PlaneGeom &g, int32_t x, int32_t y, int32_t z) {
+    return ((int64_t)z * g.ny + y) * g.wx + (x >> 5);
+}
+
+// Kernel launchers (one translation unit each).
+cudaError_t launch_voxelize_depth(const FrameArgs &a, int32_t dtype, cudaStream_t s);
+cudaError_t launch_voxelize_points(const FrameArgs &a, cudaStream_t s);
+cudaError_t configure_inflate();   // once per device, before the first launch_inflate
+cudaError_t launch_inflate(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_raytrace(const FrameArgs &a, int lanes_per_ray, cudaStream_t s);
+cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8_t *src,
+                         uint8_t *dst, cudaStream_t s);
+
+}  // namespace vg

@@ -1,0 +1,292 @@
+"""Python binding of libvg.so, the C-ABI voxel-grid library (include/vg.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Functions carry the C names; `Grid` is a small owning wrapper.
+Buffers may be torch tensors (CUDA tensors are passed as device pointers,
+CPU tensors as host pointers) or numpy arrays (host).  `stream` may be a
+torch.cuda.Stream, a raw cudaStream_t integer or None (torch's current
+stream).  There is no CPU fallback: if the library cannot be loaded every
+call raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libvg.so")
+
+VG_OK, VG_EINVAL, VG_ENOMEM, VG_ECUDA, VG_ETIMEOUT, VG_EBUSY = range(6)
+VG_UNK, VG_FREE, VG_OCC, VG_TRACED = range(4)
+VG_DEPTH_F32, VG_DEPTH_U16 = 0, 1
+VG_MEM_DEVICE, VG_MEM_HOST = 0, 1
+VG_FLAG_STATS = 1
+
+# every symbol include/vg.h declares
+EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points", "vg_shift",
+           "vg_read", "vg_write", "vg_get_origin", "vg_grid_bytes", "vg_ray_bundle", "vg_stats",
+           "vg_profile_enable", "vg_profile_read", "vg_tune", "vg_strerror")
+KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift")
+VG_TUNE_RT_LANES = 0
+
+
+class vg_params(C.Structure):
+    _fields_ = [("grid_size", C.c_int32 * 3), ("vox_size", C.c_float), ("fov_x_deg", C.c_float),
+                ("fov_y_deg", C.c_float), ("depth", C.c_float), ("vox_inf", C.c_int32),
+                ("flags", C.c_uint32)]
+
+
+class vg_stats_t(C.Structure):
+    _fields_ = [("frames", C.c_uint64), ("points_in_grid", C.c_uint64), ("ray_visits", C.c_uint64)]
+
+
+class VGError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (what, strerror(status), status))
+
+
+_LIB = None
+
+
+def load(path=None):
+    """Load libvg.so (built by paper_2112_13169_gb300.build); raise if absent."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libvg.so not found at %s: build it with paper_2112_13169_gb300.build.build()" % p)
+    L = C.CDLL(p)
+    vp, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
+    sig = {
+        "vg_create": (C.c_int, [vp, vp, vp, C.POINTER(vp)]),
+        "vg_destroy": (None, [vp]),
+        "vg_integrate_depth": (C.c_int, [vp, vp, i32, i32, i32, i32, f32, vp, vp]),
+        "vg_integrate_points": (C.c_int, [vp, vp, i32, i64, vp, vp]),
+        "vg_shift": (C.c_int, [vp, vp, vp]),
+        "vg_read": (C.c_int, [vp, vp, i32, i64, vp, vp]),
+        "vg_write": (C.c_int, [vp, vp, i32, i64, vp, vp]),
+        "vg_get_origin": (C.c_int, [vp, vp]),
+        "vg_grid_bytes": (i64, [vp]),
+        "vg_ray_bundle": (i64, [vp, vp]),
+        "vg_stats": (C.c_int, [vp, vp]),
+        "vg_profile_enable": (C.c_int, [vp, i32]),
+        "vg_profile_read": (C.c_int, [vp, vp, vp, vp, i32]),
+        "vg_tune": (C.c_int, [vp, i32, i32]),
+        "vg_strerror": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _LIB = L
+    return L
+
+
+def strerror(status):
+    try:
+        return load().vg_strerror(int(status)).decode()
+    except RuntimeError:
+        return "status %d" % status
+
+
+def _check(status, what):
+    if status != VG_OK:
+        raise VGError(status, what)
+
+
+def make_params(n, vox_size, fov_x_deg, fov_y_deg, depth, vox_inf, flags=0):
+    p = vg_params()
+    for k in range(3):
+        p.grid_size[k] = int(n[k])
+    p.vox_size = float(vox_size)
+    p.fov_x_deg = float(fov_x_deg)
+    p.fov_y_deg = float(fov_y_deg)
+    p.depth = float(depth)
+    p.vox_inf = int(vox_inf)
+    p.flags = int(flags)
+    return p
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _buffer(x):
+    """(pointer, mem kind, nbytes, dtype string) of a tensor or array."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                raise ValueError("buffer must be contiguous")
+            mem = VG_MEM_DEVICE if x.is_cuda else VG_MEM_HOST
+            return x.data_ptr(), mem, x.numel() * x.element_size(), str(x.dtype).replace("torch.", "")
+    except ImportError:
+        pass
+    a = x
+    if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+        raise ValueError("buffer must be a contiguous numpy array or torch tensor")
+    return a.ctypes.data, VG_MEM_HOST, a.nbytes, str(a.dtype)
+
+
+def _f64(v, n):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(n))
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def vg_grid_bytes(params):
+    return int(load().vg_grid_bytes(C.byref(params)))
+
+
+def vg_ray_bundle(params):
+    out = (C.c_int32 * 3)()
+    n = load().vg_ray_bundle(C.byref(params), out)
+    return (out[0], out[1], out[2]), int(n)
+
+
+def vg_create(params, robot_pos_w, stream=None):
+    h = C.c_void_p()
+    pos, pp = _f64(robot_pos_w, 3)
+    _check(load().vg_create(C.byref(params), pp, _stream(stream), C.byref(h)), "vg_create")
+    return h
+
+
+def vg_destroy(h):
+    if h:
+        load().vg_destroy(h)
+
+
+def vg_integrate_depth(h, depth, T_wc, depth_scale=1.0, stream=None):
+    ptr, mem, nbytes, dt = _buffer(depth)
+    if dt == "float32":
+        dtype = VG_DEPTH_F32
+    elif dt == "uint16":
+        dtype = VG_DEPTH_U16
+    else:
+        raise ValueError("depth must be float32 or uint16, got " + dt)
+    H, W = depth.shape
+    T, tp = _f64(T_wc, 16)
+    _check(load().vg_integrate_depth(h, C.c_void_p(ptr), mem, int(W), int(H), dtype, float(depth_scale),
+                                     tp, _stream(stream)), "vg_integrate_depth")
+
+
+def vg_integrate_points(h, xyz, T_wc, stream=None):
+    ptr, mem, nbytes, dt = _buffer(xyz)
+    if dt != "float32":
+        raise ValueError("points must be float32 xyz triples")
+    T, tp = _f64(T_wc, 16)
+    _check(load().vg_integrate_points(h, C.c_void_p(ptr), mem, nbytes // 12, tp, _stream(stream)),
+           "vg_integrate_points")
+
+
+def vg_shift(h, robot_pos_w, stream=None):
+    pos, pp = _f64(robot_pos_w, 3)
+    _check(load().vg_shift(h, pp, _stream(stream)), "vg_shift")
+
+
+def vg_read(h, dst, stream=None):
+    """Enqueue a copy of loc_grid into dst; returns the origin (int32[3])."""
+    ptr, mem, nbytes, _ = _buffer(dst)
+    o = np.zeros(3, np.int32)
+    _check(load().vg_read(h, C.c_void_p(ptr), mem, nbytes, o.ctypes.data_as(C.c_void_p), _stream(stream)),
+           "vg_read")
+    return o
+
+
+def vg_write(h, src, origin, stream=None):
+    ptr, mem, nbytes, _ = _buffer(src)
+    o = np.ascontiguousarray(np.asarray(origin, np.int32).reshape(3))
+    _check(load().vg_write(h, C.c_void_p(ptr), mem, nbytes, o.ctypes.data_as(C.c_void_p), _stream(stream)),
+           "vg_write")
+
+
+def vg_get_origin(h):
+    o = np.zeros(3, np.int32)
+    _check(load().vg_get_origin(h, o.ctypes.data_as(C.c_void_p)), "vg_get_origin")
+    return o
+
+
+def vg_stats(h):
+    s = vg_stats_t()
+    _check(load().vg_stats(h, C.byref(s)), "vg_stats")
+    return {"frames": s.frames, "points_in_grid": s.points_in_grid, "ray_visits": s.ray_visits}
+
+
+def vg_profile_enable(h, enable=True):
+    _check(load().vg_profile_enable(h, 1 if enable else 0), "vg_profile_enable")
+
+
+def vg_profile_read(h, reset=True):
+    """{kernel: (summed ms, timed launches, total launches)}; synchronises."""
+    ms = (C.c_double * 5)()
+    timed = (C.c_int64 * 5)()
+    total = (C.c_int64 * 5)()
+    _check(load().vg_profile_read(h, ms, timed, total, 1 if reset else 0), "vg_profile_read")
+    return {k: (ms[i], timed[i], total[i]) for i, k in enumerate(KERNELS)}
+
+
+def vg_tune(h, knob, value):
+    _check(load().vg_tune(h, int(knob), int(value)), "vg_tune")
+
+
+class Grid:
+    """One local grid on the current CUDA device (owns its vg_grid)."""
+
+    def __init__(self, n, vox_size, fov_x_deg, fov_y_deg, depth, vox_inf, robot_pos_w=(0, 0, 0),
+                 flags=0, stream=None):
+        self.params = make_params(n, vox_size, fov_x_deg, fov_y_deg, depth, vox_inf, flags)
+        self.n = tuple(int(v) for v in n)
+        self.shape = (self.n[2], self.n[1], self.n[0])
+        self.nvox = self.n[0] * self.n[1] * self.n[2]
+        self.h = vg_create(self.params, robot_pos_w, stream)
+
+    def integrate_depth(self, depth, T_wc, depth_scale=1.0, stream=None):
+        vg_integrate_depth(self.h, depth, T_wc, depth_scale, stream)
+
+    def integrate_points(self, xyz, T_wc, stream=None):
+        vg_integrate_points(self.h, xyz, T_wc, stream)
+
+    def shift(self, robot_pos_w, stream=None):
+        vg_shift(self.h, robot_pos_w, stream)
+
+    def read(self, dst, stream=None):
+        return vg_read(self.h, dst, stream)
+
+    def write(self, src, origin, stream=None):
+        vg_write(self.h, src, origin, stream)
+
+    @property
+    def origin(self):
+        return vg_get_origin(self.h)
+
+    def stats(self):
+        return vg_stats(self.h)
+
+    def profile(self, enable=True):
+        vg_profile_enable(self.h, enable)
+
+    def profile_read(self, reset=True):
+        return vg_profile_read(self.h, reset)
+
+    def tune(self, lanes_per_ray):
+        vg_tune(self.h, VG_TUNE_RT_LANES, lanes_per_ray)
+
+    def close(self):
+        if self.h:
+            vg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

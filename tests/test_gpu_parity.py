@@ -1,0 +1,335 @@
+"""CUDA path vs the CPU oracle, voxel by voxel, through the C ABI.
+
+The bar is bit-exact: every voxel state of loc_grid and the grid origin must
+equal the oracle's after every frame.  Any mismatch is reported with the
+voxel, both states and the count; none is tolerated.
+"""
+import numpy as np
+import pytest
+
+from oracle import OracleGrid, OracleParams
+from synth import body_pose, make
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_13169_gb300 import build
+    build.build()
+    from paper_2112_13169_gb300 import vg as vgmod
+    vgmod.load()
+    return vgmod
+
+
+def assert_same(got, ref, what):
+    bad = np.argwhere(got != ref)
+    if len(bad):
+        z, y, x = bad[0]
+        pairs = {}
+        for b in bad[:100000]:
+            k = (int(got[tuple(b)]), int(ref[tuple(b)]))
+            pairs[k] = pairs.get(k, 0) + 1
+        raise AssertionError("%s: %d voxels differ; first (x=%d, y=%d, z=%d) gpu=%d oracle=%d; "
+                             "(gpu, oracle) pair counts %s" % (what, len(bad), x, y, z, got[z, y, x],
+                                                               ref[z, y, x], pairs))
+
+
+class Pair:
+    """A GPU grid and an oracle grid driven with the same calls."""
+
+    def __init__(self, vg, n, vs, fx, fy, depth, r, pos, lanes=None, flags=0):
+        self.vg = vg
+        self.g = vg.Grid(n, vs, fx, fy, depth, r, pos, flags=flags)
+        if lanes:
+            self.g.tune(lanes)
+        self.o = OracleGrid(OracleParams(tuple(n), vs, fx, fy, depth, r), pos)
+        self.out = torch.empty(self.g.nvox, dtype=torch.uint8, device="cuda")
+
+    def depth(self, d, T, scale=1.0, device=True, check=True):
+        dd = torch.from_numpy(np.ascontiguousarray(d)).cuda() if device else np.ascontiguousarray(d)
+        self.g.integrate_depth(dd, T, scale)
+        self.o.integrate_depth(T, d, scale)
+        if check:
+            self.check("depth frame")
+
+    def points(self, xyz, T, device=True, check=True):
+        xyz = np.ascontiguousarray(xyz, np.float32)
+        self.g.integrate_points(torch.from_numpy(xyz).cuda() if device else xyz, T)
+        self.o.integrate_points(T, xyz)
+        if check:
+            self.check("point frame")
+
+    def shift(self, pos, check=True):
+        self.g.shift(pos)
+        self.o.shift(pos)
+        if check:
+            self.check("shift")
+
+    def read(self):
+        origin = self.g.read(self.out)
+        torch.cuda.synchronize()
+        return self.out.cpu().numpy().reshape(self.g.shape), origin
+
+    def check(self, what):
+        got, origin = self.read()
+        assert list(origin) == list(self.o.o), (what, origin, self.o.o)
+        assert_same(got, self.o.loc, what)
+
+    def close(self):
+        self.g.close()
+
+
+def run_workload(vg, w, nframes, lanes=None, device=True, shift=True):
+    g = w.grid
+    f0 = w.frames[0]
+    P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, f0.robot_pos, lanes)
+    try:
+        for i in range(nframes):
+            f = w.frames[i]
+            P.depth(f.depth, f.T_wc, w.cam.scale, device=device, check=False)
+            P.check("%s frame %d" % (w.name, i))
+            if shift:
+                P.shift(f.robot_pos, check=False)
+                P.check("%s shift after frame %d" % (w.name, i))
+        got, _ = P.read()
+        return got
+    finally:
+        P.close()
+
+
+# --------------------------------------------------------------------------
+# the measurement configurations
+# --------------------------------------------------------------------------
+def test_room_single_frame(vg):
+    w = make("room")
+    got = run_workload(vg, w, 1, shift=False)
+    counts = np.bincount(got.ravel(), minlength=4)
+    assert counts[1] > 1000 and counts[2] > 1000, counts   # free and occupied voxels exist
+
+
+def test_paper_shapes_sequence(vg):
+    run_workload(vg, make("paper", frames=6), 6)
+
+
+def test_sequence_full_size(vg):
+    # 640x480 f32, 200x200x100 grid at 0.05 m, vox_inf 2, shift every frame,
+    # in the launch configuration the benchmark times
+    run_workload(vg, make("seq", frames=4), 4)
+
+
+def test_hires_u16_full_size(vg):
+    run_workload(vg, make("hires", frames=2), 2)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_lanes_per_ray_do_not_change_results(vg, lanes):
+    run_workload(vg, make("paper", frames=2), 2, lanes=lanes)
+
+
+def test_host_memory_inputs(vg):
+    run_workload(vg, make("room"), 1, device=False, shift=False)
+
+
+def test_robot_mix_shapes(vg):
+    for i in range(3):
+        run_workload(vg, make("robot", robot=i, frames=2), 2)
+
+
+# --------------------------------------------------------------------------
+# edge cases
+# --------------------------------------------------------------------------
+def _pair(vg, n=(40, 36, 20), vs=0.1, fx=87.0, fy=58.0, depth=3.0, r=1, pos=(0.01, 0.02, 0.03), **kw):
+    return Pair(vg, n, vs, fx, fy, depth, r, pos, **kw)
+
+
+def test_empty_and_invalid_frames(vg):
+    P = _pair(vg)
+    T = body_pose([0.01, 0.02, 0.03], 0.3)
+    P.depth(np.zeros((24, 32), np.float32), T)
+    P.depth(np.full((24, 32), np.nan, np.float32), T)
+    d = np.full((24, 32), np.inf, np.float32)
+    d[::2] = -1.0
+    P.depth(d, T)
+    P.depth(np.full((24, 32), 3.0, np.float32), T)          # exactly the range: valid
+    P.depth(np.full((24, 32), np.nextafter(np.float32(3.0), np.float32(4.0)), np.float32), T)
+    P.close()
+
+
+@pytest.mark.parametrize("W,H", [(37, 23), (1, 1), (5, 3), (641, 479)])
+def test_ragged_images(vg, W, H):
+    rng = np.random.default_rng(W * 1000 + H)
+    P = _pair(vg)
+    d = rng.uniform(0.2, 3.5, size=(H, W)).astype(np.float32)
+    d[rng.random(d.shape) < 0.2] = 0
+    P.depth(d, body_pose([0.01, 0.02, 0.03], 0.5, 0.1, -0.1))
+    P.close()
+
+
+def test_unaligned_depth_pointer(vg):
+    rng = np.random.default_rng(5)
+    P = _pair(vg)
+    base = torch.from_numpy(rng.uniform(0.2, 3.5, size=24 * 32 + 1).astype(np.float32)).cuda()
+    view = base[1:].view(24, 32)                 # 4-byte aligned, not 16-byte aligned
+    T = body_pose([0.01, 0.02, 0.03], 0.2)
+    P.g.integrate_depth(view, T)
+    P.o.integrate_depth(T, view.cpu().numpy())
+    P.check("unaligned f32")
+    base16 = torch.from_numpy(rng.integers(0, 4000, size=24 * 32 + 1).astype(np.uint16)).cuda()
+    v16 = base16[1:].view(24, 32)
+    P.g.integrate_depth(v16, T, 0.001)
+    P.o.integrate_depth(T, v16.cpu().numpy(), 0.001)
+    P.check("unaligned u16")
+    P.close()
+
+
+@pytest.mark.parametrize("r", [0, 1, 2, 3, 7, 15])
+def test_inflation_radii(vg, r):
+    rng = np.random.default_rng(100 + r)
+    P = _pair(vg, n=(70, 50, 33), r=r)
+    d = rng.uniform(0.3, 3.0, size=(30, 40)).astype(np.float32)
+    P.depth(d, body_pose([0.01, 0.02, 0.03], 1.0, 0.2))
+    P.close()
+
+
+@pytest.mark.parametrize("n", [(1, 1, 1), (1, 17, 1), (33, 1, 2), (45, 31, 7), (31, 9, 5), (64, 64, 8),
+                               (129, 3, 4)])
+def test_grid_shapes(vg, n):
+    rng = np.random.default_rng(sum(n))
+    P = _pair(vg, n=n, vs=0.1, r=1, pos=(0.0, 0.0, 0.0))
+    for k in range(3):
+        d = rng.uniform(0.05, 3.0, size=(24, 32)).astype(np.float32)
+        P.depth(d, body_pose([0.0, 0.0, 0.0], rng.uniform(-3, 3), rng.uniform(-0.5, 0.5)))
+        P.shift(rng.uniform(-0.3, 0.3, 3))
+    P.close()
+
+
+def test_camera_outside_grid(vg):
+    rng = np.random.default_rng(9)
+    P = _pair(vg, n=(30, 30, 10), pos=(0.0, 0.0, 0.0))
+    for cam in ([-2.5, 0.1, 0.2], [0.3, 5.0, 0.0], [0.0, 0.0, 3.0]):
+        d = rng.uniform(0.5, 3.0, size=(24, 32)).astype(np.float32)
+        P.depth(d, body_pose(cam, rng.uniform(-3, 3), rng.uniform(-0.8, 0.8)))
+    P.close()
+
+
+def test_random_attitudes(vg):
+    rng = np.random.default_rng(11)
+    P = _pair(vg, n=(60, 60, 30), r=2)
+    for _ in range(6):
+        d = rng.uniform(0.2, 3.0, size=(48, 64)).astype(np.float32)
+        d[rng.random(d.shape) < 0.3] = 0
+        T = body_pose(rng.uniform(-0.2, 0.2, 3), *rng.uniform(-np.pi, np.pi, 3))
+        P.depth(d, T)
+    P.close()
+
+
+def test_axis_aligned_rays(vg):
+    # identity attitude with the camera on a voxel corner: rays along grid
+    # planes, many exact ties in the traversal
+    P = _pair(vg, n=(40, 40, 20), vs=0.25, fx=90.0, fy=90.0, depth=4.0, r=0, pos=(0.0, 0.0, 0.0))
+    P.depth(np.full((9, 9), 2.0, np.float32), np.eye(4))
+    P.depth(np.full((9, 9), 2.0, np.float32), body_pose([0.0, 0.0, 0.0]))
+    P.depth(np.zeros((9, 9), np.float32), body_pose([0.25, 0.5, 0.0], np.pi / 2))
+    P.close()
+
+
+def test_shifts(vg):
+    rng = np.random.default_rng(13)
+    P = _pair(vg, n=(30, 20, 10), pos=(0.0, 0.0, 0.0))
+    P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([0, 0, 0]))
+    pos = np.zeros(3)
+    for step in ([0.1, 0, 0], [0, -0.25, 0.1], [-0.33, 0.47, -0.2], [0, 0, 0], [2.9, 0, 0], [0, 0, 5.0],
+                 [-0.05, 0.05, 0.0]):
+        pos = pos + np.array(step)
+        P.shift(pos)
+        P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose(pos, rng.uniform(-3, 3)))
+    P.close()
+
+
+def test_point_clouds(vg):
+    rng = np.random.default_rng(17)
+    P = _pair(vg, n=(50, 40, 20), r=2)
+    pts = rng.uniform([-2, -1, 0.1], [2, 1, 3.5], size=(5000, 3)).astype(np.float32)
+    pts[::97, 0] = np.nan
+    pts[::89, 2] = np.inf
+    P.points(pts, body_pose([0.01, 0.02, 0.03], 0.4))
+    P.points(pts[:1], body_pose([0.01, 0.02, 0.03], -0.4))
+    P.points(np.zeros((0, 3), np.float32), body_pose([0.01, 0.02, 0.03], 2.0))
+    P.points(pts, body_pose([0.01, 0.02, 0.03], 1.0), device=False)
+    P.close()
+
+
+def test_read_write_roundtrip_and_resume(vg):
+    rng = np.random.default_rng(19)
+    P = _pair(vg, n=(40, 30, 16))
+    prior = rng.integers(0, 4, size=P.g.shape).astype(np.uint8)
+    origin = np.array([-17, -11, -9], np.int32)
+    P.g.write(torch.from_numpy(prior.ravel().copy()).cuda(), origin)
+    P.o.loc = prior.copy()
+    P.o.o = origin.copy()
+    P.check("after write")
+    P.g.write(prior.ravel().copy(), origin)         # host source
+    P.check("after host write")
+    pos = (origin + np.array([20, 15, 8])) * 0.1 + 0.01
+    P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose(pos, 0.7))
+    host = np.empty(P.g.nvox, np.uint8)
+    o = P.g.read(host)
+    torch.cuda.synchronize()
+    assert_same(host.reshape(P.g.shape), P.o.loc, "host read")
+    assert list(o) == list(P.o.o)
+    P.close()
+
+
+def test_stats_count_points_and_visits(vg, orc):
+    from oracle import OracleParams as OP
+    rng = np.random.default_rng(23)
+    n, vs, r = (50, 40, 20), 0.1, 1
+    P = _pair(vg, n=n, vs=vs, r=r, flags=vg.VG_FLAG_STATS)
+    d = rng.uniform(0.2, 3.5, size=(24, 32)).astype(np.float32)
+    T = body_pose([0.01, 0.02, 0.03], 0.3)
+    P.depth(d, T)
+    s = P.g.stats()
+    p = OP(n, vs, 87.0, 58.0, 3.0, r)
+    pose = orc.pose_vc(p, T, P.o.o)
+    raw, kept = orc.voxelize_depth(p, pose, d)
+    _, _, visits = orc.raytrace(p, pose, orc.inflate(p, raw))
+    assert s["frames"] == 1 and s["points_in_grid"] == kept and s["ray_visits"] == visits, (s, kept, visits)
+    P.close()
+
+
+def test_profile_counts_launches(vg):
+    w = make("paper", frames=3)
+    g = w.grid
+    grid = vg.Grid(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos)
+    grid.profile(True)
+    for f in w.frames:
+        grid.integrate_depth(torch.from_numpy(f.depth).cuda(), f.T_wc)
+        grid.shift(f.robot_pos)
+    prof = grid.profile_read()
+    for k in ("voxelize", "inflate", "raytrace", "merge"):
+        ms, timed, total = prof[k]
+        assert timed == 3 and total == 3 and ms > 0, (k, prof[k])
+    grid.close()
+
+
+def test_bad_arguments_on_device(vg):
+    P = _pair(vg)
+    d = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(vg.VGError) as e:
+        P.g.integrate_depth(d, np.full((4, 4), np.nan))
+    assert e.value.status == vg.VG_EINVAL
+    with pytest.raises(vg.VGError):
+        P.g.integrate_depth(torch.zeros((4, 4), dtype=torch.uint16, device="cuda"), np.eye(4), depth_scale=0.0)
+    with pytest.raises(ValueError):
+        P.g.integrate_depth(torch.zeros((4, 4), dtype=torch.float64, device="cuda"), np.eye(4))
+    with pytest.raises(vg.VGError):
+        P.g.tune(3)
+    small = torch.empty(10, dtype=torch.uint8, device="cuda")
+    with pytest.raises(vg.VGError):
+        P.g.read(small)
+    P.close()
