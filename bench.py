@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0, help="K3 lanes per ray (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle sample budget")
+    ap.add_argument("--preroll", type=float, default=1.0, help="seconds of untimed frames before timing")
     return ap.parse_args()
 
 
@@ -271,7 +272,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_pre = time.time()
     k = 0
-    while time.time() - t_pre < 1.0:
+    while time.time() - t_pre < args.preroll:
         step(grid, k)
         k += 1
         if k % 50 == 0:

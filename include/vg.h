@@ -21,7 +21,10 @@
  *    image holds z-depth.  The world and the grid are ENU-aligned (Sec. IV-A).
  *  - T_wc: row-major 4x4 double, camera optical frame -> world (T^w_c of
  *    Table I).  The library composes T^v_c = T^v_w T^w_c on the host in
- *    double and rounds it to float once (Sec. IV-B).
+ *    double and rounds it to float once (Sec. IV-B).  A pose is rejected
+ *    (VG_EINVAL) if any entry is not finite, if an entry of its rotation
+ *    block lies outside [-1.5, 1.5], or if the camera is 2^22 voxels or
+ *    more from the grid's corner voxel.
  *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
  *    Calls are asynchronous with respect to the host unless stated; inputs
  *    must stay valid until the enqueued work completes.  Calls on one grid
@@ -217,7 +220,9 @@ VG_API int vg_profile_read(vg_grid *grid, double ms[VG_NKERNELS], int64_t timed[
 /*
  * Tuning knobs (defaults are set by vg_create):
  *  VG_TUNE_RT_LANES  lanes of a warp that share one ray in K3: 1, 2, 4, 8,
- *                    16 or 32 (default 8).  Results do not depend on it.
+ *                    16 or 32, or 0 for automatic (the default: the fewest
+ *                    lanes, at least 8, whose share of the longest ray fits
+ *                    the per-lane visit buffer).  Results do not depend on it.
  * Errors: VG_EINVAL.
  */
 enum { VG_TUNE_RT_LANES = 0 };

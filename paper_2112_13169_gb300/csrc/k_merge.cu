@@ -78,29 +78,45 @@ __global__ void __launch_bounds__(256) k_shift(const PlaneGeom g, const int32_t 
     int32_t x = (int32_t)(i0 % g.nx);
     int64_t yz = i0 / g.nx;
     int32_t y = (int32_t)(yz % g.ny), z = (int32_t)(yz / g.ny);
-    uint8_t out[16];
+    // which of the 16 voxels have a source voxel
+    uint32_t valid = 0;
 #pragma unroll
     for (int b = 0; b < 16; ++b) {
-        uint8_t v = 0;
         const int32_t sx = x + dx, sy = y + dy, sz = z + dz;
         if (i0 + b < g.nvox && (unsigned)sx < (unsigned)g.nx && (unsigned)sy < (unsigned)g.ny &&
             (unsigned)sz < (unsigned)g.nz)
-            v = __ldg(src + i0 + b + off);
-        out[b] = v;
+            valid |= 1u << b;
         if (++x == g.nx) {
             x = 0;
             if (++y == g.ny) { y = 0; ++z; }
         }
     }
-    if (i0 + 16 <= g.nvox) {
-        uint4 q;
-        q.x = out[0] | (out[1] << 8) | (out[2] << 16) | ((uint32_t)out[3] << 24);
-        q.y = out[4] | (out[5] << 8) | (out[6] << 16) | ((uint32_t)out[7] << 24);
-        q.z = out[8] | (out[9] << 8) | (out[10] << 16) | ((uint32_t)out[11] << 24);
-        q.w = out[12] | (out[13] << 8) | (out[14] << 16) | ((uint32_t)out[15] << 24);
-        *reinterpret_cast<uint4 *>(dst + i0) = q;
+    uint32_t o[4];
+    if (valid == 0xffffu) {
+        // all sources exist: bytes [sb, sb+16) of src, 0 <= sb and sb+15 < nvox,
+        // read as five aligned words; the last may reach up to 4 bytes past
+        // nvox, into the slack the host leaves after every loc buffer, and
+        // those bytes are shifted out
+        const int64_t sb = i0 + off;
+        const uint32_t *wsrc = reinterpret_cast<const uint32_t *>(src + (sb & ~int64_t(3)));
+        const int sh = (int)(sb & 3) * 8;
+        uint32_t wv[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) wv[m] = __ldg(wsrc + m);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) o[m] = __funnelshift_r(wv[m], wv[m + 1], sh);
     } else {
-        for (int b = 0; b < 16 && i0 + b < g.nvox; ++b) dst[i0 + b] = out[b];
+        uint8_t ob[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) ob[b] = ((valid >> b) & 1u) ? __ldg(src + i0 + b + off) : (uint8_t)0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            o[m] = ob[4 * m] | (ob[4 * m + 1] << 8) | (ob[4 * m + 2] << 16) | ((uint32_t)ob[4 * m + 3] << 24);
+    }
+    if (i0 + 16 <= g.nvox) {
+        *reinterpret_cast<uint4 *>(dst + i0) = make_uint4(o[0], o[1], o[2], o[3]);
+    } else {
+        for (int b = 0; b < 16 && i0 + b < g.nvox; ++b) dst[i0 + b] = (uint8_t)(o[b >> 2] >> (8 * (b & 3)));
     }
 }
 

@@ -5,9 +5,9 @@
 // the valid ones with the pinhole model, transforms them by T^v_c and sets
 // their voxel's bit in the occ_raw plane.  Neighbouring pixels mostly land
 // in the same 32-voxel word, so each warp de-duplicates its words with
-// ballots and one OR-reduction before a single atomicOr per distinct word:
-// the plane is bit-packed, so concurrent sets need an atomic, but only once
-// per word per warp.
+// a segmented OR-scan across lanes before one atomicOr per run of lanes
+// that share a word: the plane is bit-packed, so concurrent sets need an
+// atomic, but only about one per distinct word per warp.
 //
 // Arithmetic follows the oracle's order with one IEEE rounding per operation
 // (explicit __f*_rn intrinsics; this file is also built with -fmad=false):
@@ -48,19 +48,24 @@ __device__ __forceinline__ uint32_t pixel_word(const FrameArgs &a, float d, int3
     return point_word(a, xc, yc, d, bit);
 }
 
-// OR `bit` into plane[key] once per distinct key of the warp.  Every lane of
-// the warp must call this (keys of idle lanes are kNoWord).
+// ORs `bit` into plane[key] for every lane, with one atomicOr per run of
+// consecutive lanes that share a word (neighbouring pixels usually do): an
+// inclusive OR-scan over lanes that only pulls from lanes with the same key,
+// after which the last lane of each run holds the run's bits.  Lanes whose
+// keys match but are not adjacent may fold bits into each other; that is
+// harmless, they name the same word.  Every lane of the warp must call this
+// (keys of idle lanes are kNoWord).
 __device__ __forceinline__ void warp_set_bits(uint32_t *plane, uint32_t key, uint32_t bit) {
     const int lane = threadIdx.x & 31;
-    unsigned pending = __ballot_sync(kFull, key != kNoWord);
-    while (pending) {
-        const int leader = __ffs(pending) - 1;
-        const uint32_t k = __shfl_sync(kFull, key, leader);
-        const bool same = (key == k);
-        const uint32_t bits = __reduce_or_sync(kFull, same ? bit : 0u);
-        if (lane == leader) atomicOr(plane + k, bits);
-        pending &= ~__ballot_sync(kFull, same);
+    uint32_t v = bit;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t kd = __shfl_up_sync(kFull, key, d);
+        const uint32_t vd = __shfl_up_sync(kFull, v, d);
+        if (lane >= d && kd == key) v |= vd;
     }
+    const uint32_t knext = __shfl_down_sync(kFull, key, 1);
+    if (key != kNoWord && (lane == 31 || knext != key)) atomicOr(plane + key, v);
 }
 
 // Adds the warp's number of in-grid points to the stats counter.  Every lane

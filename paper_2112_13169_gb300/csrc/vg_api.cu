@@ -102,7 +102,9 @@ struct Layout {
 Layout layout_of(const PlaneGeom &g) {
     Layout L;
     size_t off = 0;
-    const size_t locb = align256((size_t)g.nvox), planeb = align256((size_t)g.words * 4);
+    // 16 bytes of slack after each loc buffer: K5's vector path may read up
+    // to 4 bytes past the last voxel (and discards them)
+    const size_t locb = align256((size_t)g.nvox + 16), planeb = align256((size_t)g.words * 4);
     L.loc = off; off += locb;
     L.loc_alt = off; off += locb;
     L.occ_raw = off; off += planeb;
@@ -126,13 +128,23 @@ void origin_of(const vg_params *p, const double pos[3], int32_t o[3]) {
         o[k] = (int32_t)floor(pos[k] / (double)p->vox_size) - p->grid_size[k] / 2;
 }
 
+// Composes T^v_c.  Rejects poses that are not finite, whose rotation block
+// has an entry outside [-1.5, 1.5] (no rotation does), or whose camera lies
+// 2^22 voxels or more from the grid corner: K3's walk length is bounded by
+// the ray's length in voxels, and these limits keep it bounded and keep
+// FP32 voxel coordinates exact to well below one voxel.
 bool pose_of(const vg_grid *G, const double T_wc[16], vg::Pose32 &T) {
     if (!T_wc) return false;
     for (int i = 0; i < 16; ++i)
         if (!std::isfinite(T_wc[i])) return false;
     for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) T.R[r * 3 + c] = (float)T_wc[r * 4 + c];
-        T.t[r] = (float)(T_wc[r * 4 + 3] - (double)G->origin[r] * (double)G->p.vox_size);
+        for (int c = 0; c < 3; ++c) {
+            if (!(std::fabs(T_wc[r * 4 + c]) <= 1.5)) return false;
+            T.R[r * 3 + c] = (float)T_wc[r * 4 + c];
+        }
+        const double t = T_wc[r * 4 + 3] - (double)G->origin[r] * (double)G->p.vox_size;
+        if (!(std::fabs(t / (double)G->p.vox_size) < 4194304.0)) return false;
+        T.t[r] = (float)t;
     }
     return true;
 }
@@ -156,7 +168,11 @@ cudaError_t g_config_err[64];
 
 cudaError_t configure_device(int dev) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::call_once(g_configured[dev], [dev] { g_config_err[dev] = vg::configure_inflate(); });
+    std::call_once(g_configured[dev], [dev] {
+        cudaError_t e = vg::configure_inflate();
+        if (e == cudaSuccess) e = vg::configure_raytrace(dev);
+        g_config_err[dev] = e;
+    });
     return g_config_err[dev];
 }
 
@@ -225,7 +241,8 @@ cudaError_t finish_frame(vg_grid *G, FrameArgs &a, cudaStream_t s) {
     } else {
         a.pl.occ_inf = a.pl.occ_raw;   // no inflation: the raw plane is the inflated one
     }
-    e = launch(G, VG_K_RAYTRACE, s, [&] { return vg::launch_raytrace(a, G->lanes_per_ray, s); });
+    const int lpr = G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh);
+    e = launch(G, VG_K_RAYTRACE, s, [&] { return vg::launch_raytrace(a, lpr, s); });
     if (e != cudaSuccess) return e;
     return launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge(a, s); });
 }
@@ -267,7 +284,7 @@ int vg_create(const vg_params *params, const double robot_pos_w[3], void *stream
     G->g = geom_of(params);
     origin_of(params, robot_pos_w, G->origin);
     bundle_of(params, G->vd, G->hw, G->hh);
-    G->lanes_per_ray = 8;
+    G->lanes_per_ray = 0;   // automatic
     cudaError_t e = cudaGetDevice(&G->device);
     if (e == cudaSuccess) e = configure_device(G->device);
     const Layout L = layout_of(G->g);
@@ -356,7 +373,7 @@ int vg_profile_read(vg_grid *G, double ms[VG_NKERNELS], int64_t timed[VG_NKERNEL
 int vg_tune(vg_grid *G, int32_t knob, int32_t value) {
     if (!G) return VG_EINVAL;
     if (knob == VG_TUNE_RT_LANES) {
-        if (value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
             return VG_EINVAL;
         G->lanes_per_ray = value;
         return VG_OK;

@@ -1,7 +1,8 @@
 // vg_internal.cuh -- types shared by the kernels and the host library.
 //
 // Device data layout of one grid (one cudaMalloc, carved in this order):
-//   loc      Nx*Ny*Nz bytes, the paper's index order idx = x + y*Nx + z*Nx*Ny
+//   loc      Nx*Ny*Nz bytes, the paper's index order idx = x + y*Nx + z*Nx*Ny,
+//            followed by at least 16 bytes of slack
 //   loc_alt  the same size; target of the out-of-place shift (ping-pong)
 //   occ_raw, occ_inf, fr, tr
 //            bit planes of the measurement grid.  Bit b of word
@@ -18,6 +19,7 @@
 namespace vg {
 
 constexpr int kMaxInflate = 15;
+constexpr int kRtBuf = 24;   // in-grid visits a K3 lane keeps in shared memory
 
 struct PlaneGeom {
     int32_t nx, ny, nz;
@@ -69,6 +71,8 @@ cudaError_t launch_voxelize_depth(const FrameArgs &a, int32_t dtype, cudaStream_
 cudaError_t launch_voxelize_points(const FrameArgs &a, cudaStream_t s);
 cudaError_t configure_inflate();   // once per device, before the first launch_inflate
 cudaError_t launch_inflate(const FrameArgs &a, cudaStream_t s);
+cudaError_t configure_raytrace(int dev);   // once per device, before the first launch_raytrace
+int auto_lanes_per_ray(int32_t vd, int32_t hw, int32_t hh);
 cudaError_t launch_raytrace(const FrameArgs &a, int lanes_per_ray, cudaStream_t s);
 cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s);
 cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8_t *src,

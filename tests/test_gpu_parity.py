@@ -126,9 +126,27 @@ def test_hires_u16_full_size(vg):
     run_workload(vg, make("hires", frames=2), 2)
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8, 16, 32])
 def test_lanes_per_ray_do_not_change_results(vg, lanes):
+    # 0 is automatic; 1, 2 and 4 lanes overflow the per-lane visit buffer on
+    # most rays and take the two-pass walk
     run_workload(vg, make("paper", frames=2), 2, lanes=lanes)
+
+
+def test_lanes_on_full_size_sequence(vg):
+    for lanes in (4, 32):
+        run_workload(vg, make("seq", frames=2), 2, lanes=lanes)
+
+
+def test_huge_plane_takes_the_unbuffered_walk(vg):
+    # 1 x 4096 x 4096 voxels: 2^26 plane words, too many for a packed visit,
+    # so every lane walks twice instead of buffering
+    rng = np.random.default_rng(29)
+    P = Pair(vg, (1, 4096, 4096), 0.1, 87.0, 58.0, 1.0, 1, (0.0, 0.0, 0.0))
+    d = rng.uniform(0.2, 1.2, size=(24, 32)).astype(np.float32)
+    P.depth(d, body_pose([0.0, 0.0, 0.0], np.pi / 2))   # looking along +y, inside the 1-voxel slab
+    P.depth(d, body_pose([0.0, 0.0, 0.0], np.pi / 2, 0.3))
+    P.close()
 
 
 def test_host_memory_inputs(vg):
