@@ -12,6 +12,8 @@
 // always recomputed from the integer face; the next crossing is the smallest
 // t, the lowest axis on a tie; the walk ends at the first crossing >= 1.
 // The start voxel floor(S) is visited.  Voxels outside the grid are skipped.
+// 1/D_k is taken with the correctly rounded reciprocal, which is the IEEE
+// quotient 1/D_k; the face coordinate is kept as an exact float.
 //
 // Free-space rule (Alg. 2): voxels before the ray's first occupied voxel
 // (of the inflated plane) are marked free, voxels after it
@@ -21,108 +23,129 @@
 // depend on the order rays run in.
 //
 // Parallel walk.  LPR lanes of a warp share one ray.  Lane j owns the face
-// crossings with tau in [c_j, c_{j+1}), c_0 = -inf, c_LPR = 1, c_j = j/LPR
-// otherwise.  Because each axis's crossing times are non-decreasing in m,
+// crossings with tau in [c_j, c_{j+1}), c_0 = -inf, c_LPR = 1, and the
+// other cuts split the part of the segment inside the grid evenly.  Because each axis's crossing times are non-decreasing in m,
 // the serial walk performs exactly the crossings with t < c_j before any
 // other, so lane j starts from voxel floor(S) + step * n(c_j), with
 // n_k(c) = #{m : t_k(m) < c} found by an estimate and an exact fix-up on
 // the same float expression, and then merges the three axes exactly as the
 // serial walk does.  The lanes' visit lists concatenate to the serial list.
 //
-// Pass 1: each lane walks its slice and stops at its first occupied voxel.
-// A ballot over the ray's lanes gives the first lane F that met one.
-// Pass 2: each lane walks again and marks: lanes before F all free; lane F
-// free before its occupied voxel and traced after it; lanes after F traced.
-// Marks after the first occupied voxel are written without re-reading the
-// occupancy: a traced mark on an occupied voxel is overridden by K4.  Marks
-// that fall in the same 32-voxel word are OR-ed in a register and flushed
-// with one atomicOr; near the camera, where all rays overlap, they go to a
-// per-CTA shared-memory box first (see kBoxW).
+// Pass 1: each lane walks its slice once and keeps its in-grid visits in
+// its own shared-memory column (kRtBuf entries), then finds the first
+// occupied one, kChunk occupancy words in flight at a time.  A ballot over
+// the ray's lanes gives the first lane F that met one.
+// Pass 2: each lane replays its visits and marks: lanes before F all free;
+// lane F free before its occupied voxel and traced after it; lanes after F
+// traced.  Marks after the first occupied voxel are written without
+// re-reading the occupancy: a traced mark on an occupied voxel is
+// overridden by K4.  Marks that fall in the same 32-voxel word are OR-ed in
+// a register and flushed with one atomicOr; near the camera, where all rays
+// overlap, they go to a per-CTA shared-memory box first (see kBoxW).
+// A lane whose slice holds more than kRtBuf in-grid visits, or a grid whose
+// planes are too large for a packed visit, walks twice instead.
+//
+// The CTAs are persistent: each loops over groups of kThreads / LPR rays,
+// so the box is staged and flushed once per CTA.
 #include "vg_internal.cuh"
-
-#include <cfloat>
 
 namespace vg {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kChunk = 4;   // occupancy words loaded together
+constexpr int kThreads = 256;
 
-struct Axis {
-    float S;       // start, voxel units
-    float inv;     // 1 / D, 0 when inactive
-    int32_t b0;    // first face crossed
-    int32_t step;  // -1, 0, +1
+// The box around the camera voxel: kBoxW plane words (x) by kBoxY rows by
+// kBoxZ slices.  Its occupancy words are staged in shared memory once per
+// CTA and its free/traced marks are OR-ed there, then flushed once per CTA.
+constexpr int kBoxW = 2, kBoxY = 16, kBoxZ = 16;
+constexpr int kBoxWords = kBoxW * kBoxY * kBoxZ;
+
+// A visit packed in 32 bits: bit 31 set -> box word (index in bits 5..),
+// else the plane bit index P = ((z*ny + y) * 32*wx + x) < 2^31; bits 0..4
+// are x & 31 either way, so p >> 5 is the word.
+constexpr uint32_t kBoxFlag = 0x80000000u;
+
+struct Box {
+    int32_t bw0, by0, bz0;
 };
 
-__device__ __forceinline__ float cross_t(const Axis &ax, int32_t m) {
-    return __fmul_rn(__fsub_rn((float)(ax.b0 + ax.step * m), ax.S), ax.inv);
-}
-
-// Number of crossings of this axis with t < c (c finite, > 0).
-__device__ __forceinline__ int32_t crossings_before(const Axis &ax, float D, float c) {
-    if (ax.step == 0) return 0;
-    const float t0 = cross_t(ax, 0);
-    if (!(t0 < c)) return 0;
-    float est = __fmul_rn(__fsub_rn(c, t0), fabsf(D));
-    int32_t m = est < 1.0e7f ? (int32_t)est + 1 : 10000000;
-    while (m > 1 && !(cross_t(ax, m - 1) < c)) --m;
-    while (cross_t(ax, m) < c) ++m;
-    return m;
-}
-
-// Walker state of one lane: voxel (i0, i1, i2), next crossing times
-// (t0, t1, t2), and the voxel's plane word and bit, kept up to date
-// incrementally (w = (i2*ny + i1)*wx + (i0 >> 5), xb = i0 & 31).
-struct Walker {
-    int32_t i0, i1, i2;
-    float t0, t1, t2;
-    uint32_t w;   // modulo 2^32 while outside the grid; exact inside it
-    int32_t xb;
-};
-
+// Per-ray constants of one lane.
 struct Ray {
-    Axis ax[3];
-    int32_t dw1, dw2;   // word-index change of one y / z step
+    float S[3];      // start, voxel units
+    float inv[3];    // 1/D, 0 for an inactive axis
+    float fs[3];     // step as float
+    int32_t s[3];    // step: -1, 0, +1
+    int32_t dP[3];   // change of the plane bit index per step
     int32_t nx, ny, nz;
 };
 
-__device__ __forceinline__ void walker_init(Walker &w, const Ray &r, const int32_t n0[3], int32_t wx) {
-    w.i0 = (int32_t)floorf(r.ax[0].S) + r.ax[0].step * n0[0];
-    w.i1 = (int32_t)floorf(r.ax[1].S) + r.ax[1].step * n0[1];
-    w.i2 = (int32_t)floorf(r.ax[2].S) + r.ax[2].step * n0[2];
-    w.t0 = r.ax[0].step ? cross_t(r.ax[0], n0[0]) : INFINITY;
-    w.t1 = r.ax[1].step ? cross_t(r.ax[1], n0[1]) : INFINITY;
-    w.t2 = r.ax[2].step ? cross_t(r.ax[2], n0[2]) : INFINITY;
-    w.w = ((uint32_t)w.i2 * (uint32_t)r.ny + (uint32_t)w.i1) * (uint32_t)wx + (uint32_t)(w.i0 >> 5);
-    w.xb = w.i0 & 31;
+struct Walker {
+    float t0, t1, t2;     // next crossing time per axis
+    float nb0, nb1, nb2;  // coordinate of the next face per axis (exact)
+    int32_t i0, i1, i2;   // voxel
+    uint32_t P;           // plane bit index, modulo 2^32 outside the grid
+};
+
+__device__ __forceinline__ float cross_at(float b, float S, float inv) {
+    return __fmul_rn(__fsub_rn(b, S), inv);
+}
+
+// Number of crossings of axis k with t < c (c finite, > 0).
+__device__ __forceinline__ int32_t crossings_before(const Ray &r, int k, float absD, float c) {
+    if (r.s[k] == 0) return 0;
+    const int32_t b0 = (int32_t)floorf(r.S[k]) + (r.s[k] > 0 ? 1 : 0);
+    const float t0 = cross_at((float)b0, r.S[k], r.inv[k]);
+    if (!(t0 < c)) return 0;
+    const float est = __fmul_rn(__fsub_rn(c, t0), absD);
+    int32_t m = est < 1.0e7f ? (int32_t)est + 1 : 10000000;
+    while (m > 1 && !(cross_at((float)(b0 + r.s[k] * (m - 1)), r.S[k], r.inv[k]) < c)) --m;
+    while (cross_at((float)(b0 + r.s[k] * m), r.S[k], r.inv[k]) < c) ++m;
+    return m;
+}
+
+__device__ __forceinline__ void walker_init(Walker &w, const Ray &r, const int32_t n0[3], uint32_t R) {
+    w.i0 = (int32_t)floorf(r.S[0]) + r.s[0] * n0[0];
+    w.i1 = (int32_t)floorf(r.S[1]) + r.s[1] * n0[1];
+    w.i2 = (int32_t)floorf(r.S[2]) + r.s[2] * n0[2];
+    w.nb0 = (float)(w.i0 + (r.s[0] > 0 ? 1 : 0));
+    w.nb1 = (float)(w.i1 + (r.s[1] > 0 ? 1 : 0));
+    w.nb2 = (float)(w.i2 + (r.s[2] > 0 ? 1 : 0));
+    w.t0 = r.s[0] ? cross_at(w.nb0, r.S[0], r.inv[0]) : INFINITY;
+    w.t1 = r.s[1] ? cross_at(w.nb1, r.S[1], r.inv[1]) : INFINITY;
+    w.t2 = r.s[2] ? cross_at(w.nb2, r.S[2], r.inv[2]) : INFINITY;
+    w.P = ((uint32_t)w.i2 * (uint32_t)r.ny + (uint32_t)w.i1) * R + (uint32_t)w.i0;
 }
 
 // Advances to the next voxel if the next crossing is before c_hi.  The axis
-// with the smallest tMax moves, the lowest axis on a tie: x iff
-// t0 <= t1 and t0 <= t2, else y iff t1 <= t2, else z.  Branch-free, so the
-// lanes of a warp stepping different axes do not diverge.
+// with the smallest tMax moves, the lowest axis on a tie: x iff t0 is the
+// minimum, else y iff t1 is, else z.  The three updates are short, mutually
+// exclusive blocks, so lanes stepping different axes do not diverge.
 __device__ __forceinline__ bool walker_next(Walker &w, const Ray &r, float c_hi) {
-    const bool mx = (w.t0 <= w.t1) && (w.t0 <= w.t2);
-    const bool my = !mx && (w.t1 <= w.t2);
-    const bool mz = !mx && !my;
-    const float tm = mx ? w.t0 : (my ? w.t1 : w.t2);
+    const float tm = fminf(w.t0, fminf(w.t1, w.t2));
     if (!(tm < c_hi)) return false;
-    const int32_t s0 = mx ? r.ax[0].step : 0;
-    w.i0 += s0;
-    w.i1 += my ? r.ax[1].step : 0;
-    w.i2 += mz ? r.ax[2].step : 0;
-    int32_t xb = w.xb + s0;
-    const int32_t carry = (xb >> 5);          // +1 when xb reached 32, -1 when it went below 0
-    w.xb = xb & 31;
-    w.w += (uint32_t)(carry + (my ? r.dw1 : 0) + (mz ? r.dw2 : 0));
-    const int32_t ik = mx ? w.i0 : (my ? w.i1 : w.i2);
-    const int32_t sk = mx ? r.ax[0].step : (my ? r.ax[1].step : r.ax[2].step);
-    const float Sk = mx ? r.ax[0].S : (my ? r.ax[1].S : r.ax[2].S);
-    const float ik_inv = mx ? r.ax[0].inv : (my ? r.ax[1].inv : r.ax[2].inv);
-    const float nt = __fmul_rn(__fsub_rn((float)(ik + (sk > 0 ? 1 : 0)), Sk), ik_inv);
-    w.t0 = mx ? nt : w.t0;
-    w.t1 = my ? nt : w.t1;
-    w.t2 = mz ? nt : w.t2;
+    const bool mx = (w.t0 == tm);
+    const bool my = !mx && (w.t1 == tm);
+    const bool mz = !mx && !my;
+    if (mx) {
+        w.i0 += r.s[0];
+        w.P += (uint32_t)r.dP[0];
+        w.nb0 = __fadd_rn(w.nb0, r.fs[0]);
+        w.t0 = cross_at(w.nb0, r.S[0], r.inv[0]);
+    }
+    if (my) {
+        w.i1 += r.s[1];
+        w.P += (uint32_t)r.dP[1];
+        w.nb1 = __fadd_rn(w.nb1, r.fs[1]);
+        w.t1 = cross_at(w.nb1, r.S[1], r.inv[1]);
+    }
+    if (mz) {
+        w.i2 += r.s[2];
+        w.P += (uint32_t)r.dP[2];
+        w.nb2 = __fadd_rn(w.nb2, r.fs[2]);
+        w.t2 = cross_at(w.nb2, r.S[2], r.inv[2]);
+    }
     return true;
 }
 
@@ -133,40 +156,20 @@ __device__ __forceinline__ bool in_grid(const Walker &w, const Ray &r) {
 
 // True when an out-of-grid axis can no longer come back.
 __device__ __forceinline__ bool gone(const Walker &w, const Ray &r) {
-    return (w.i0 < 0 && r.ax[0].step <= 0) || (w.i0 >= r.nx && r.ax[0].step >= 0) ||
-           (w.i1 < 0 && r.ax[1].step <= 0) || (w.i1 >= r.ny && r.ax[1].step >= 0) ||
-           (w.i2 < 0 && r.ax[2].step <= 0) || (w.i2 >= r.nz && r.ax[2].step >= 0);
+    return (w.i0 < 0 && r.s[0] <= 0) || (w.i0 >= r.nx && r.s[0] >= 0) || (w.i1 < 0 && r.s[1] <= 0) ||
+           (w.i1 >= r.ny && r.s[1] >= 0) || (w.i2 < 0 && r.s[2] <= 0) || (w.i2 >= r.nz && r.s[2] >= 0);
 }
-
-constexpr int kChunk = 4;   // occupancy words loaded together
-constexpr int kThreads = 256;
-
-// Near the camera every ray of the bundle crosses the same few voxels.  A
-// box of kBoxW plane words (x) by kBoxY rows by kBoxZ slices around the
-// camera voxel is kept in shared memory by every CTA: the occupancy words
-// are staged there once, and free/traced marks inside the box are OR-ed
-// there and flushed to the planes once per CTA.
-constexpr int kBoxW = 2, kBoxY = 32, kBoxZ = 32;
-constexpr int kBoxWords = kBoxW * kBoxY * kBoxZ;
-
-// A visit packed in 32 bits: bit 31 set -> shared-box word (index in bits
-// 5..15), else plane word w (< 2^26) in bits 5..30; bits 0..4 are x & 31.
-constexpr uint32_t kBoxFlag = 0x80000000u;
-
-struct Box {
-    int32_t bw0, by0, bz0;
-};
 
 __device__ __forceinline__ uint32_t pack_visit(const Walker &w, const Box &b) {
     const uint32_t dw = (uint32_t)((w.i0 >> 5) - b.bw0), dy = (uint32_t)(w.i1 - b.by0),
                    dz = (uint32_t)(w.i2 - b.bz0);
     if (dw < kBoxW && dy < kBoxY && dz < kBoxZ)
-        return kBoxFlag | (((dz * kBoxY + dy) * kBoxW + dw) << 5) | (uint32_t)w.xb;
-    return (w.w << 5) | (uint32_t)w.xb;
+        return kBoxFlag | (((dz * kBoxY + dy) * kBoxW + dw) << 5) | ((uint32_t)w.i0 & 31u);
+    return w.P;
 }
 
 __device__ __forceinline__ uint32_t occ_word(const FrameArgs &a, const uint32_t *occ_box, uint32_t p) {
-    return (p & kBoxFlag) ? occ_box[(p >> 5) & 0x7ffu] : __ldg(a.pl.occ_inf + (p >> 5));
+    return (p & kBoxFlag) ? occ_box[(p >> 5) & (kBoxWords - 1)] : __ldg(a.pl.occ_inf + (p >> 5));
 }
 
 // Pending marks of one lane: consecutive marks of the same word and kind
@@ -181,7 +184,7 @@ struct Marks {
 __device__ __forceinline__ void marks_flush(const FrameArgs &a, uint32_t *box_fr, uint32_t *box_tr,
                                             const Marks &m) {
     if (!m.bits) return;
-    if (m.key & (kBoxFlag >> 5)) atomicOr((m.traced ? box_tr : box_fr) + (m.key & 0x7ffu), m.bits);
+    if (m.key & (kBoxFlag >> 5)) atomicOr((m.traced ? box_tr : box_fr) + (m.key & (kBoxWords - 1)), m.bits);
     else atomicOr((m.traced ? a.pl.tr : a.pl.fr) + m.key, m.bits);
 }
 
@@ -197,13 +200,12 @@ __device__ __forceinline__ void marks_add(const FrameArgs &a, uint32_t *box_fr, 
     m.bits |= 1u << (p & 31u);
 }
 
-// Two-pass walk for a lane whose slice does not fit its buffer: pass 1
-// returns the index (among the slice's in-grid visits) of the first
-// occupied voxel, or -1.
+// Two-pass walk for a lane whose slice does not fit its buffer: returns the
+// index (among the slice's in-grid visits) of the first occupied voxel, or -1.
 __device__ int walk_first_hit(const FrameArgs &a, const Ray &r, const int32_t n0[3], bool visit_start,
-                              float c_hi, const Box &b, const uint32_t *occ_box) {
+                              float c_hi, const Box &b, const uint32_t *occ_box, uint32_t R) {
     Walker w;
-    walker_init(w, r, n0, a.g.wx);
+    walker_init(w, r, n0, R);
     bool more = visit_start ? true : walker_next(w, r, c_hi);
     int32_t q = 0;
     while (more) {
@@ -239,9 +241,9 @@ __device__ int walk_first_hit(const FrameArgs &a, const Ray &r, const int32_t n0
 // Pass 2 of the two-pass walk: marks the slice's in-grid visits.
 __device__ unsigned walk_marks(const FrameArgs &a, const Ray &r, const int32_t n0[3], bool visit_start,
                                float c_hi, const Box &b, int mode, int32_t hit_at, uint32_t *box_fr,
-                               uint32_t *box_tr) {
+                               uint32_t *box_tr, uint32_t R) {
     Walker w;
-    walker_init(w, r, n0, a.g.wx);
+    walker_init(w, r, n0, R);
     bool more = visit_start ? true : walker_next(w, r, c_hi);
     int32_t q = 0;
     Marks m;
@@ -260,19 +262,16 @@ __device__ unsigned walk_marks(const FrameArgs &a, const Ray &r, const int32_t n
     return (unsigned)q;
 }
 
-// kBuf visits per lane are kept in dynamic shared memory (column-major,
-// one column per thread) when `buffered` is set; lanes whose slice holds
-// more use the two-pass walk.  Persistent: each CTA loops over groups of
-// kThreads / LPR rays.
 template <int LPR>
 __global__ void __launch_bounds__(kThreads) k_raytrace(const FrameArgs a, const int buffered) {
     __shared__ uint32_t box_fr[kBoxWords], box_tr[kBoxWords], occ_box[kBoxWords];
-    extern __shared__ uint32_t buf[];   // kRtBuf * kThreads
+    extern __shared__ uint32_t buf[];   // kRtBuf * kThreads, one column per thread
 
     const int lane = threadIdx.x & 31;
     const int j = lane & (LPR - 1);
     const int32_t width = 2 * a.hw + 1;
     const int64_t nrays = (int64_t)width * (2 * a.hh + 1);
+    const uint32_t R = 32u * (uint32_t)a.g.wx;   // plane bits per row
     float S[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) S[k] = __fdiv_rn(a.T.t[k], a.vs);
@@ -308,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) k_raytrace(const FrameArgs a, const 
         r.nx = a.g.nx;
         r.ny = a.g.ny;
         r.nz = a.g.nz;
-        float D[3];
+        float absD[3];
         {
             const int32_t ra = active ? (int32_t)(ray % width) - a.hw : 0;
             const int32_t rb = active ? (int32_t)(ray / width) - a.hh : 0;
@@ -318,30 +317,52 @@ __global__ void __launch_bounds__(kThreads) k_raytrace(const FrameArgs a, const 
                 const float d = __fadd_rn(__fadd_rn(__fmul_rn(a.T.R[k * 3 + 0], fa),
                                                     __fmul_rn(a.T.R[k * 3 + 1], fb)),
                                           __fmul_rn(a.T.R[k * 3 + 2], fvd));
-                D[k] = d;
-                r.ax[k].S = S[k];
-                r.ax[k].inv = 0.0f;
-                r.ax[k].step = 0;
+                absD[k] = fabsf(d);
+                r.S[k] = S[k];
+                r.inv[k] = 0.0f;
+                r.s[k] = 0;
                 if (d != 0.0f) {
-                    const float q = __fdiv_rn(1.0f, d);
+                    const float q = __frcp_rn(d);
                     if (isfinite(q)) {
-                        r.ax[k].inv = q;
-                        r.ax[k].step = d > 0.0f ? 1 : -1;
+                        r.inv[k] = q;
+                        r.s[k] = d > 0.0f ? 1 : -1;
                     }
                 }
-                r.ax[k].b0 = (int32_t)floorf(S[k]) + (r.ax[k].step > 0 ? 1 : 0);
+                r.fs[k] = (float)r.s[k];
             }
+            r.dP[0] = r.s[0];
+            r.dP[1] = r.s[1] * (int32_t)R;
+            r.dP[2] = r.s[2] * (int32_t)R * a.g.ny;
         }
-        r.dw1 = r.ax[1].step * a.g.wx;
-        r.dw2 = r.ax[2].step * a.g.wx * a.g.ny;
 
-        // this lane's slice of tau
-        const float c_lo = (float)j / (float)LPR;   // exact: LPR is a power of two
-        const float c_hi = (j == LPR - 1) ? 1.0f : (float)(j + 1) / (float)LPR;
+        // this lane's slice of tau: the in-grid part of the segment is cut
+        // into LPR equal pieces (any cuts give the same visits as long as
+        // neighbouring lanes agree on them and the last lane ends at 1)
+        float c_lo, c_hi;
+        {
+            float ts = 0.0f, te = 1.0f;
+            const float nk[3] = {(float)a.g.nx, (float)a.g.ny, (float)a.g.nz};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (r.s[k] != 0) {
+                    const float t_lo = __fmul_rn(__fsub_rn(r.s[k] > 0 ? 0.0f : nk[k], S[k]), r.inv[k]);
+                    const float t_hi = __fmul_rn(__fsub_rn(r.s[k] > 0 ? nk[k] : 0.0f, S[k]), r.inv[k]);
+                    ts = fmaxf(ts, t_lo);
+                    te = fminf(te, t_hi);
+                }
+            }
+            if (!(te > ts)) {
+                ts = 0.0f;
+                te = 1.0f;
+            }
+            const float span = __fsub_rn(te, ts);
+            c_lo = __fadd_rn(ts, __fmul_rn(span, (float)j / (float)LPR));
+            c_hi = (j == LPR - 1) ? 1.0f : __fadd_rn(ts, __fmul_rn(span, (float)(j + 1) / (float)LPR));
+        }
         int32_t n0[3] = {0, 0, 0};
         if (j > 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) n0[k] = crossings_before(r.ax[k], D[k], c_lo);
+            for (int k = 0; k < 3; ++k) n0[k] = crossings_before(r, k, absD[k], c_lo);
         }
 
         // ---- pass 1: walk the slice once, keep its in-grid visits --------
@@ -349,7 +370,7 @@ __global__ void __launch_bounds__(kThreads) k_raytrace(const FrameArgs a, const 
         bool ovf = !buffered;
         if (active && !ovf) {
             Walker w;
-            walker_init(w, r, n0, a.g.wx);
+            walker_init(w, r, n0, R);
             bool more = (j == 0) ? true : walker_next(w, r, c_hi);
             while (more) {
                 if (in_grid(w, r)) {
@@ -376,7 +397,7 @@ __global__ void __launch_bounds__(kThreads) k_raytrace(const FrameArgs a, const 
                     if (q0 + c < nvis && ((v[c] >> (p[c] & 31u)) & 1u)) hit_at = q0 + c;
             }
         }
-        if (active && ovf) hit_at = walk_first_hit(a, r, n0, j == 0, c_hi, b, occ_box);
+        if (active && ovf) hit_at = walk_first_hit(a, r, n0, j == 0, c_hi, b, occ_box, R);
 
         // ---- first lane of this ray with an occupied voxel ---------------
         const unsigned hits = __ballot_sync(kFull, hit_at >= 0);
@@ -397,7 +418,7 @@ __global__ void __launch_bounds__(kThreads) k_raytrace(const FrameArgs a, const 
             marks_flush(a, box_fr, box_tr, m);
             visits += (unsigned)nvis;
         } else if (active) {
-            visits += walk_marks(a, r, n0, j == 0, c_hi, b, mode, hit_at, box_fr, box_tr);
+            visits += walk_marks(a, r, n0, j == 0, c_hi, b, mode, hit_at, box_fr, box_tr, R);
         }
     }
 
@@ -442,7 +463,7 @@ cudaError_t launch_lpr(const FrameArgs &a, int idx, cudaStream_t s) {
     const int64_t resident = (int64_t)g_sms[dev] * (g_blocks_per_sm[dev][idx] > 0 ? g_blocks_per_sm[dev][idx] : 1);
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
     if (blocks == 0) return cudaSuccess;
-    // packed visits hold a plane word in 26 bits
+    // a packed visit holds a plane bit index below 2^31
     const int buffered = a.g.words < (int64_t(1) << 26) ? 1 : 0;
     k_raytrace<LPR><<<blocks, kThreads, sizeof(uint32_t) * kRtBuf * kThreads, s>>>(a, buffered);
     return cudaGetLastError();

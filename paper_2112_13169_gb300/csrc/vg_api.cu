@@ -87,7 +87,8 @@ PlaneGeom geom_of(const vg_params *p) {
     g.ny = p->grid_size[1];
     g.nz = p->grid_size[2];
     const int32_t w = (g.nx + 31) / 32;
-    g.wx = (w + 3) / 4 * 4;
+    g.wx = 4;
+    while (g.wx < w) g.wx *= 2;
     g.words = (int64_t)g.wx * g.ny * g.nz;
     g.nvox = (int64_t)g.nx * g.ny * g.nz;
     return g;

@@ -6,9 +6,10 @@
 //   loc_alt  the same size; target of the out-of-place shift (ping-pong)
 //   occ_raw, occ_inf, fr, tr
 //            bit planes of the measurement grid.  Bit b of word
-//            (z*Ny + y)*WX + w is voxel x = 32*w + b of row (y, z).  WX is
-//            ceil(Nx/32) rounded up to a multiple of 4 words so every row
-//            starts on a 16-byte boundary.  Bits with x >= Nx stay 0.
+//            (z*Ny + y)*WX + w is voxel x = 32*w + b of row (y, z), i.e.
+//            plane bit (z*Ny + y)*32*WX + x.  WX is ceil(Nx/32) rounded up
+//            to a power of two, at least 4 words, so every row starts on a
+//            16-byte boundary.  Bits with x >= Nx stay 0.
 //   stats    three u64 counters (VG_FLAG_STATS)
 // The planes are all-zero between frames: K4 clears every word it reads.
 #pragma once
@@ -19,7 +20,9 @@
 namespace vg {
 
 constexpr int kMaxInflate = 15;
-constexpr int kRtBuf = 24;   // in-grid visits a K3 lane keeps in shared memory
+// In-grid visits a K3 lane keeps in shared memory.  36 entries (36 KB per
+// 256-thread CTA plus 6 KB of box) let five CTAs share an SM.
+constexpr int kRtBuf = 36;
 
 struct PlaneGeom {
     int32_t nx, ny, nz;
