@@ -230,6 +230,29 @@ def algorithmic_bytes(kind, w, geom):
             "shift": 2 * nvox}[kind]
 
 
+# One serial Amanatides-Woo step of the paper's ray trace with its
+# occupancy test and mark: argmin of three tMax (2 compares, 2 selects),
+# loop-end compare, index step, face step, tMax recompute (sub, mul),
+# in-grid test (3 compares), linear index step, bit test (shift, and),
+# mark (or).
+OPS_PER_VISIT = 16
+
+
+def raytrace_traffic():
+    """DRAM bytes per K3 launch from the committed ncu record, or None when
+    the kernel source changed since it was taken."""
+    import hashlib
+    rec = os.path.join(ROOT, "profiles", "k_raytrace_dram.json")
+    src = os.path.join(ROOT, "paper_2112_13169_gb300", "csrc", "k_raytrace.cu")
+    try:
+        d = json.load(open(rec))
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() == d["source_sha256"]:
+            return d["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def run_ours(args):
     import torch
     from paper_2112_13169_gb300 import build as vgbuild
@@ -360,10 +383,22 @@ def run_ours(args):
         v["share"] = v["avg_us"] * v["launches"] / tot
     dom = max(kern, key=lambda k: kern[k]["avg_us"] * kern[k]["launches"])
     d = kern[dom]
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
-                "frac": d["gbs"] / hbm_peak, "traffic": None, "peak_source": peak_kind,
-                "alg_bytes_per_launch": d["alg_bytes"], "avg_us": d["avg_us"]}
     visits_per_frame = st["ray_visits"] / max(1, st["frames"])
+    if dom == "raytrace":
+        # issue-bound: ops model of one serial DDA step with its test and mark,
+        # against every lane of every SM issuing once per cycle at max clock
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak_tops = sms * 128 * mhz * 1e6 / 1e12
+        achieved = visits_per_frame * OPS_PER_VISIT / (d["avg_us"] * 1e-6) / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                    "frac": achieved / peak_tops, "traffic": raytrace_traffic(),
+                    "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (sms, mhz, peak_kind),
+                    "ops_per_visit": OPS_PER_VISIT, "visits_per_launch": visits_per_frame, "avg_us": d["avg_us"]}
+    else:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": d["gbs"] / hbm_peak, "traffic": None, "peak_source": peak_kind,
+                    "alg_bytes_per_launch": d["alg_bytes"], "avg_us": d["avg_us"]}
 
     cpu = None
     if not args.no_cpu_baseline:
