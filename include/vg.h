@@ -59,7 +59,8 @@ enum {
     VG_ENOMEM = 2,   /* device or host allocation failed */
     VG_ECUDA = 3,    /* a CUDA call failed (including an earlier asynchronous fault) */
     VG_ETIMEOUT = 4, /* a bounded device wait ran out */
-    VG_EBUSY = 5     /* resource in use */
+    VG_EBUSY = 5,    /* resource in use */
+    VG_ESCRATCH = 6  /* the request needs more than the library's fixed scratch array */
 };
 
 /* Voxel states stored in loc_grid. */
@@ -227,6 +228,42 @@ VG_API int vg_profile_read(vg_grid *grid, double ms[VG_NKERNELS], int64_t timed[
  */
 enum { VG_TUNE_RT_LANES = 0 };
 VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
+
+/*
+ * One measurement without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code that must never block in the driver's allocator (a
+ * real-time control loop), integrations that hand out all device memory
+ * themselves, or processes whose allocator belongs to another runtime.
+ *
+ * It does what vg_integrate_depth does (K1 voxelize, K2 inflate, K3
+ * ray-trace, K4 merge) for a grid the caller owns, without a vg_grid:
+ *  params     grid parameters, as for vg_create (flags are ignored).
+ *  origin     the grid's origin (voxel index of voxel (0,0,0) in the world
+ *             lattice), e.g. as vg_read reports it; the caller keeps it.
+ *  loc        device pointer to the caller's loc_grid, Nx*Ny*Nz bytes in
+ *             the layout above, read and updated in place; 16-byte aligned.
+ *  depth, width, height, dtype, depth_scale, T_wc, stream
+ *             as for vg_integrate_depth, with depth a device pointer.
+ * The four measurement bit planes live in one array of 16 MiB compiled into
+ * the library (every GPU that loads the library holds it until the process
+ * exits).  A grid whose plane needs more than 2^20 32-bit words
+ * (ceil(Nx/32) rounded up to a power of two, at least 4, times Ny*Nz) is
+ * refused with VG_ESCRATCH before any device work.  No cudaMalloc,
+ * cudaFree or other allocating call is made.
+ * The first call on a device does a one-time set-up there (it looks up the
+ * array's device address and configures the kernels); make that first call
+ * before any stream capture.  Every call shares the array and clears the
+ * part it uses on its stream before using it, so calls whose device work
+ * overlaps -- on different streams or from different host threads -- race
+ * and corrupt each other's results; serialise them.
+ * Errors: VG_EINVAL (NULL, bad size or pose, unaligned loc), VG_ESCRATCH,
+ * VG_ECUDA.
+ */
+VG_API int vg_integrate_depth_noalloc(const vg_params *params, const int32_t origin[3],
+                                      uint8_t *loc, const void *depth, int32_t width,
+                                      int32_t height, int32_t dtype, float depth_scale,
+                                      const double T_wc[16], void *stream);
 
 /* Static description of a status code. */
 VG_API const char *vg_strerror(int status);

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvg.so")
 
-SOURCES = ["vg_api.cu", "k_voxelize.cu", "k_inflate.cu", "k_raytrace.cu", "k_merge.cu"]
+SOURCES = ["vg_api.cu", "k_voxelize.cu", "k_inflate.cu", "k_raytrace.cu", "k_merge.cu", "vg_noalloc.cu"]
 NO_FMAD = {"k_voxelize.cu", "k_raytrace.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

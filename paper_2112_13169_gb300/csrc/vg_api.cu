@@ -260,6 +260,7 @@ const char *vg_strerror(int status) {
     case VG_ECUDA: return "CUDA error";
     case VG_ETIMEOUT: return "device wait timed out";
     case VG_EBUSY: return "busy";
+    case VG_ESCRATCH: return "grid too large for the fixed scratch array";
     default: return "unknown status";
     }
 }

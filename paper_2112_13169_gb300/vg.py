@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvg.so")
 
-VG_OK, VG_EINVAL, VG_ENOMEM, VG_ECUDA, VG_ETIMEOUT, VG_EBUSY = range(6)
+VG_OK, VG_EINVAL, VG_ENOMEM, VG_ECUDA, VG_ETIMEOUT, VG_EBUSY, VG_ESCRATCH = range(7)
 VG_UNK, VG_FREE, VG_OCC, VG_TRACED = range(4)
 VG_DEPTH_F32, VG_DEPTH_U16 = 0, 1
 VG_MEM_DEVICE, VG_MEM_HOST = 0, 1
@@ -25,7 +25,7 @@ VG_FLAG_STATS = 1
 # every symbol include/vg.h declares
 EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points", "vg_shift",
            "vg_read", "vg_write", "vg_get_origin", "vg_grid_bytes", "vg_ray_bundle", "vg_stats",
-           "vg_profile_enable", "vg_profile_read", "vg_tune", "vg_strerror")
+           "vg_profile_enable", "vg_profile_read", "vg_tune", "vg_strerror", "vg_integrate_depth_noalloc")
 KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift")
 VG_TUNE_RT_LANES = 0
 
@@ -75,6 +75,7 @@ def load(path=None):
         "vg_profile_read": (C.c_int, [vp, vp, vp, vp, i32]),
         "vg_tune": (C.c_int, [vp, i32, i32]),
         "vg_strerror": (C.c_char_p, [C.c_int]),
+        "vg_integrate_depth_noalloc": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, f32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -177,6 +178,33 @@ def vg_integrate_depth(h, depth, T_wc, depth_scale=1.0, stream=None):
     T, tp = _f64(T_wc, 16)
     _check(load().vg_integrate_depth(h, C.c_void_p(ptr), mem, int(W), int(H), dtype, float(depth_scale),
                                      tp, _stream(stream)), "vg_integrate_depth")
+
+
+def vg_integrate_depth_noalloc(params, origin, loc, depth, T_wc, depth_scale=1.0, stream=None):
+    """One measurement into a caller-owned loc grid (a CUDA uint8 tensor of
+    Nx*Ny*Nz bytes, updated in place) without any device allocation: for
+    callers that cannot allocate device memory.  The library keeps the
+    measurement planes in a fixed 16 MiB array shared by all calls, so calls
+    whose device work overlaps race; see include/vg.h."""
+    lptr, lmem, lbytes, ldt = _buffer(loc)
+    dptr, dmem, dbytes, dt = _buffer(depth)
+    if lmem != VG_MEM_DEVICE or dmem != VG_MEM_DEVICE:
+        raise ValueError("loc and depth must be device buffers")
+    n = params.grid_size
+    if ldt != "uint8" or lbytes != n[0] * n[1] * n[2]:
+        raise ValueError("loc must hold Nx*Ny*Nz uint8 voxels")
+    if dt == "float32":
+        dtype = VG_DEPTH_F32
+    elif dt == "uint16":
+        dtype = VG_DEPTH_U16
+    else:
+        raise ValueError("depth must be float32 or uint16, got " + dt)
+    H, W = depth.shape
+    o = np.ascontiguousarray(np.asarray(origin, np.int32).reshape(3))
+    T, tp = _f64(T_wc, 16)
+    _check(load().vg_integrate_depth_noalloc(C.byref(params), o.ctypes.data_as(C.c_void_p), C.c_void_p(lptr),
+                                             C.c_void_p(dptr), int(W), int(H), dtype, float(depth_scale), tp,
+                                             _stream(stream)), "vg_integrate_depth_noalloc")
 
 
 def vg_integrate_points(h, xyz, T_wc, stream=None):
