@@ -194,6 +194,90 @@ VG_API int64_t vg_ray_bundle(const vg_params *params, int32_t out[3]);
 /* Counters (VG_FLAG_STATS); synchronises the device. */
 VG_API int vg_stats(vg_grid *grid, vg_stats_t *out);
 
+/*
+ * Batched form: many measurements, each into its own grid, in one
+ * persistent fused launch (the paper processes one frame at a time).  A batch owns a device descriptor table of `capacity` frames and a
+ * pinned host copy of it.
+ *
+ * One frame of a batch: what vg_integrate_depth takes, plus an optional
+ * re-centre (vg_shift) after the merge.  depth must be device memory.
+ */
+typedef struct {
+    vg_grid *grid;          /* the frame's grid; at most one frame per grid in a batch */
+    const void *depth;      /* device pointer, W x H row-major */
+    int32_t width, height;
+    int32_t dtype;          /* VG_DEPTH_F32 or VG_DEPTH_U16 */
+    float depth_scale;      /* VG_DEPTH_U16 only */
+    double T_wc[16];        /* camera pose, as for vg_integrate_depth */
+    int32_t recentre;       /* nonzero: re-centre on robot_pos_w after the merge */
+    int32_t pad;
+    double robot_pos_w[3];
+} vg_frame;
+
+typedef struct vg_batch vg_batch;
+
+/*
+ * Creates a batch for up to `capacity` frames (1 .. 65536) on the current
+ * device: one device allocation and one pinned host allocation.
+ * Errors: VG_EINVAL, VG_ENOMEM, VG_ECUDA.
+ */
+VG_API int vg_batch_create(int32_t capacity, vg_batch **out);
+
+/* Frees the batch (synchronises the device first).  NULL is accepted. */
+VG_API void vg_batch_destroy(vg_batch *batch);
+
+/*
+ * Host-only half of a step: validates the n frames and writes their
+ * descriptors into the batch's pinned table, and applies the grids'
+ * host-side state changes (origin and buffer swap of every re-centred
+ * grid).  Waits for the previous step's table copy, so the table can be
+ * rewritten.  Grids must have vox_inf <= 3 and live on the batch's device.
+ * Errors: VG_EINVAL (bad frame, two frames for one grid, n > capacity),
+ * VG_ECUDA.
+ */
+VG_API int vg_batch_prepare(vg_batch *batch, const vg_frame *frames, int32_t n);
+
+/*
+ * Device half of a step: copies the table to the device and launches the
+ * fused kernel on `stream` (cooperative launch: K1, K2, K3, K4 and the
+ * re-centre of every prepared frame, with a grid-wide barrier between
+ * phases).  Can be captured in a CUDA graph; replaying the graph runs
+ * whatever vg_batch_prepare wrote last.  Errors: VG_EINVAL, VG_ECUDA.
+ */
+VG_API int vg_batch_enqueue(vg_batch *batch, void *stream);
+
+/* vg_batch_prepare followed by vg_batch_enqueue. */
+VG_API int vg_batch_step(vg_batch *batch, const vg_frame *frames, int32_t n, void *stream);
+
+/*
+ * Waits for the last enqueued step and reports how it ended: VG_OK, or
+ * VG_ETIMEOUT if a grid barrier gave up waiting (the step's grids are then
+ * incomplete), or VG_ECUDA.
+ */
+VG_API int vg_batch_status(vg_batch *batch);
+
+/*
+ * Batch knobs:
+ *  VG_TUNE_BATCH_CTAS_PER_SM  CTAs per SM of the fused launch, 1 .. the
+ *                             occupancy limit, or 0 for the limit (default).
+ *  VG_TUNE_BATCH_LANES        lanes per ray for every frame: 8, 16 or 32, or
+ *                             0 to use each grid's own setting (default).
+ * Results do not depend on them.  Errors: VG_EINVAL.
+ */
+enum { VG_TUNE_BATCH_CTAS_PER_SM = 100, VG_TUNE_BATCH_LANES = 101 };
+VG_API int vg_batch_tune(vg_batch *batch, int32_t knob, int32_t value);
+
+/*
+ * Autotuner: times `reps` steps of the given frames for every candidate
+ * setting of the knobs above (re-centring switched off, so every timed step
+ * merges the same measurements into the grids, which leaves them as one
+ * step would), keeps the fastest setting in the batch and writes it to
+ * best[2] = {ctas_per_sm, lanes} (may be NULL).  Synchronises the device.
+ * Errors: as vg_batch_step, VG_ETIMEOUT.
+ */
+VG_API int vg_batch_autotune(vg_batch *batch, const vg_frame *frames, int32_t n, int32_t reps,
+                             void *stream, int32_t best[2]);
+
 /* Kernels of one measurement, for profiling and launch counts. */
 enum {
     VG_K_VOXELIZE = 0, /* K1 */

@@ -18,8 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvg.so")
 
-SOURCES = ["vg_api.cu", "k_voxelize.cu", "k_inflate.cu", "k_raytrace.cu", "k_merge.cu", "vg_noalloc.cu"]
-NO_FMAD = {"k_voxelize.cu", "k_raytrace.cu"}
+SOURCES = ["vg_api.cu", "k_voxelize.cu", "k_inflate.cu", "k_raytrace.cu", "k_merge.cu", "k_batch.cu",
+           "vg_noalloc.cu"]
+NO_FMAD = {"k_voxelize.cu", "k_raytrace.cu", "k_batch.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -50,7 +51,8 @@ def build(force=False, verbose=False):
     """Compile and link libvg.so if any source changed; return its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, "vg_internal.cuh"), os.path.join(ROOT, "include", "vg.h")]
+    headers = [os.path.join(CSRC, h) for h in ("vg_internal.cuh", "vg_units.cuh", "vg_rt.cuh")]
+    headers.append(os.path.join(ROOT, "include", "vg.h"))
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

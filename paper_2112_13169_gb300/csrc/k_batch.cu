@@ -1,0 +1,209 @@
+// k_batch.cu -- many measurements in one persistent, fused launch.
+//
+// One cooperative launch of k_batch runs, for every frame of a batch (each
+// with its own grid, resolution, voxel size and radius), the whole path:
+//   phase 1  K1 voxelize           units of 1024 pixels
+//   phase 2  K2 inflate            8 x 8 x 8-word tiles (radius 1..3)
+//   phase 3  K3 ray trace          groups of 256 / LPR rays
+//   phase 4  K4 merge              256 plane words
+//   phase 5  K5 re-centre          4096 voxels (frames that shift only)
+// with a grid-wide barrier between phases.  Units of every frame are laid
+// end to end per phase (BatchItem::off), so a CTA picks a unit, finds its
+// frame by binary search and runs the same device code as the one-step
+// kernels (vg_units.cuh, vg_rt.cuh).  Reads of data an earlier phase wrote
+// skip the L1 (LoadL2).
+//
+// The barrier waits with a clock64 deadline: if the other CTAs do not all
+// arrive within a few seconds, the waiting CTA sets BatchCtl::error and
+// every CTA leaves the kernel, so the host sees VG_ETIMEOUT instead of a
+// hung GPU.  The launch is cooperative, so all CTAs are resident together.
+#include "vg_rt.cuh"
+
+namespace vg {
+namespace {
+
+using namespace rt;
+
+constexpr int kDynWords = kRtBuf * kThreads;   // also covers an inflate tile of radius <= 3
+static_assert(units::inflate_smem_words<3, 8, 8, 8>(3) <= (size_t)kDynWords, "inflate tile fits");
+
+__device__ __forceinline__ int find_item(const BatchItem *items, int n, int phase, int64_t u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {   // last item whose offset is <= u
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&items[mid].off[phase]) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Grid-wide barrier with a deadline.  Returns false (for every thread of
+// the CTA) when the batch has failed.
+__device__ bool grid_sync(BatchCtl *ctl, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = &ctl->bar_gen;
+        volatile unsigned *err = &ctl->error;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (*err || clock64() - t0 > kBarrierCycles) {
+                    atomicExch(&ctl->error, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        if (*err) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int LPR>
+__device__ __forceinline__ unsigned group_lpr(const BatchItem &it, const float S[3], const Box &b, int64_t grp,
+                                              uint32_t *box_fr, uint32_t *box_tr, const uint32_t *occ_box,
+                                              uint32_t *buf) {
+    return rt_group<LPR, units::LoadL2>(it.a, S, b, grp, it.buffered, box_fr, box_tr, occ_box, buf);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restrict__ items, BatchCtl *ctl) {
+    __shared__ uint32_t box_fr[kBoxWords], box_tr[kBoxWords], occ_box[kBoxWords];
+    extern __shared__ uint32_t dyn[];
+    const int n = ctl->n;
+    const unsigned nb = gridDim.x;
+
+    // ---- phase 1: voxelize ------------------------------------------------
+    for (int64_t u = blockIdx.x; u < ctl->total[0]; u += nb) {
+        const int i = find_item(items, n, 0, u);
+        const BatchItem &it = items[i];
+        const int64_t t = (u - it.off[0]) * kThreads + threadIdx.x;
+        if (it.dtype == 0) {
+            if (it.vec) units::voxelize_depth_thread<0, true>(it.a, t);
+            else units::voxelize_depth_thread<0, false>(it.a, t);
+        } else {
+            if (it.vec) units::voxelize_depth_thread<1, true>(it.a, t);
+            else units::voxelize_depth_thread<1, false>(it.a, t);
+        }
+    }
+    if (!grid_sync(ctl, nb)) return;
+
+    // ---- phase 2: inflate -------------------------------------------------
+    for (int64_t u = blockIdx.x; u < ctl->total[1]; u += nb) {
+        const int i = find_item(items, n, 1, u);
+        const BatchItem &it = items[i];
+        const int64_t local = u - it.off[1];
+        const int tx = (int)(local % it.tiles[0]);
+        const int ty = (int)((local / it.tiles[0]) % it.tiles[1]);
+        const int tz = (int)(local / ((int64_t)it.tiles[0] * it.tiles[1]));
+        const PlaneGeom &g = it.a.g;
+        if (it.txw == 8) {
+            switch (it.a.r) {
+            case 1: units::inflate_tile<1, 8, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
+            case 2: units::inflate_tile<2, 8, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
+            default: units::inflate_tile<3, 8, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
+            }
+        } else {
+            switch (it.a.r) {
+            case 1: units::inflate_tile<1, 4, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
+            case 2: units::inflate_tile<2, 4, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
+            default: units::inflate_tile<3, 4, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
+            }
+        }
+    }
+    if (!grid_sync(ctl, nb)) return;
+
+    // ---- phase 3: ray trace -----------------------------------------------
+    // a contiguous run of units per CTA, so the camera box is staged again
+    // only when the run crosses into another frame
+    {
+        const int64_t total = ctl->total[2];
+        const int64_t lo = total * blockIdx.x / nb, hi = total * (blockIdx.x + 1) / nb;
+        int cur = -1;
+        float S[3] = {0.0f, 0.0f, 0.0f};
+        Box b = {0, 0, 0};
+        for (int64_t u = lo; u < hi; ++u) {
+            const int i = find_item(items, n, 2, u);
+            const BatchItem &it = items[i];
+            if (i != cur) {
+                if (cur >= 0) box_flush(items[cur].a, b, box_fr, box_tr);
+                cur = i;
+                frame_start(it.a, S);
+                b = box_of(S);
+                box_stage<units::LoadL2>(it.a, b, box_fr, box_tr, occ_box);
+            }
+            const int64_t grp = u - it.off[2];
+            unsigned visits;
+            switch (it.lpr) {
+            case 8: visits = group_lpr<8>(it, S, b, grp, box_fr, box_tr, occ_box, dyn); break;
+            case 16: visits = group_lpr<16>(it, S, b, grp, box_fr, box_tr, occ_box, dyn); break;
+            default: visits = group_lpr<32>(it, S, b, grp, box_fr, box_tr, occ_box, dyn); break;
+            }
+            if (it.a.stats) {
+                const unsigned total = __reduce_add_sync(kFull, visits);
+                if ((threadIdx.x & 31) == 0 && total) atomicAdd(it.a.stats + 2, (unsigned long long)total);
+            }
+        }
+        if (cur >= 0) box_flush(items[cur].a, b, box_fr, box_tr);
+    }
+    if (!grid_sync(ctl, nb)) return;
+
+    // ---- phase 4: merge ---------------------------------------------------
+    for (int64_t u = blockIdx.x; u < ctl->total[3]; u += nb) {
+        const int i = find_item(items, n, 3, u);
+        const BatchItem &it = items[i];
+        const int64_t w = (u - it.off[3]) * kThreads + threadIdx.x;
+        if (it.align8) units::merge_word<true, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
+        else units::merge_word<false, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
+    }
+    if (ctl->total[4] == 0) return;
+    if (!grid_sync(ctl, nb)) return;
+
+    // ---- phase 5: re-centre -----------------------------------------------
+    for (int64_t u = blockIdx.x; u < ctl->total[4]; u += nb) {
+        const int i = find_item(items, n, 4, u);
+        const BatchItem &it = items[i];
+        const int64_t c = (u - it.off[4]) * kThreads + threadIdx.x;
+        units::shift_chunk<units::LoadL2>(it.a.g, it.dx, it.dy, it.dz, it.a.loc, it.loc_dst, c);
+    }
+}
+
+int g_batch_blocks_per_sm[64];
+int g_batch_sms[64];
+
+}  // namespace
+
+cudaError_t configure_batch(int dev) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const size_t dyn = sizeof(uint32_t) * kDynWords;
+    cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_batch_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_batch_blocks_per_sm[dev], k_batch, kThreads, dyn);
+    return e;
+}
+
+int batch_max_blocks(int dev) {
+    if (dev < 0 || dev >= 64) return 0;
+    return g_batch_sms[dev] * g_batch_blocks_per_sm[dev];
+}
+
+cudaError_t launch_batch(const BatchItem *items, BatchCtl *ctl, int blocks, cudaStream_t s) {
+    void *args[] = {(void *)&items, (void *)&ctl};
+    return cudaLaunchCooperativeKernel((const void *)k_batch, dim3(blocks), dim3(kThreads), args,
+                                       sizeof(uint32_t) * kDynWords, s);
+}
+
+}  // namespace vg

@@ -15,8 +15,10 @@
 #include "vg_internal.cuh"
 
 #include <cmath>
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -45,6 +47,21 @@ struct vg_grid {
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_kind;
     size_t prof_used;
+};
+
+struct vg_batch {
+    int32_t capacity;
+    int device;
+    int ctas_per_sm;    // 0: occupancy limit
+    int lanes;          // 0: each grid's own
+    uint8_t *dev;       // BatchCtl followed by capacity BatchItems
+    uint8_t *host;      // pinned copy
+    size_t bytes;       // bytes of the table to copy (set by prepare)
+    cudaEvent_t copied; // the table copy of the last enqueue
+    cudaEvent_t done;   // the kernel of the last enqueue
+    bool enqueued;
+    bool prepared;
+    uint64_t launches;
 };
 
 namespace {
@@ -172,6 +189,7 @@ cudaError_t configure_device(int dev) {
     std::call_once(g_configured[dev], [dev] {
         cudaError_t e = vg::configure_inflate();
         if (e == cudaSuccess) e = vg::configure_raytrace(dev);
+        if (e == cudaSuccess) e = vg::configure_batch(dev);
         g_config_err[dev] = e;
     });
     return g_config_err[dev];
@@ -213,6 +231,21 @@ FrameArgs frame_args(vg_grid *G, const vg::Pose32 &T) {
     a.pl = G->pl;
     a.loc = G->loc;
     a.stats = (G->p.flags & VG_FLAG_STATS) ? G->stats : nullptr;
+    return a;
+}
+
+// FrameArgs of a depth frame: the pinhole intrinsics from the field of view.
+FrameArgs depth_frame_args(vg_grid *G, const vg::Pose32 &T, const void *depth, int32_t width, int32_t height,
+                           int32_t dtype, float depth_scale) {
+    FrameArgs a = frame_args(G, T);
+    a.depth = depth;
+    a.W = width;
+    a.H = height;
+    a.scale = (dtype == VG_DEPTH_U16) ? depth_scale : 1.0f;
+    a.fx = (float)(((double)width / 2.0) / tan(half_fov(G->p.fov_x_deg)));
+    a.fy = (float)(((double)height / 2.0) / tan(half_fov(G->p.fov_y_deg)));
+    a.cx = (float)(((double)width - 1.0) / 2.0);
+    a.cy = (float)(((double)height - 1.0) / 2.0);
     return a;
 }
 
@@ -401,15 +434,7 @@ int vg_integrate_depth(vg_grid *G, const void *depth, int32_t mem, int32_t width
         int rc = stage_input(G, depth, bytes, s, &dptr);
         if (rc != VG_OK) return rc;
     }
-    FrameArgs a = frame_args(G, T);
-    a.depth = dptr;
-    a.W = width;
-    a.H = height;
-    a.scale = (dtype == VG_DEPTH_U16) ? depth_scale : 1.0f;
-    a.fx = (float)(((double)width / 2.0) / tan(half_fov(G->p.fov_x_deg)));
-    a.fy = (float)(((double)height / 2.0) / tan(half_fov(G->p.fov_y_deg)));
-    a.cx = (float)(((double)width - 1.0) / 2.0);
-    a.cy = (float)(((double)height - 1.0) / 2.0);
+    FrameArgs a = depth_frame_args(G, T, dptr, width, height, dtype, depth_scale);
     cudaError_t e = launch(G, VG_K_VOXELIZE, s, [&] { return vg::launch_voxelize_depth(a, dtype, s); });
     if (e == cudaSuccess) e = finish_frame(G, a, s);
     if (e != cudaSuccess) return status_of(e);
@@ -511,6 +536,242 @@ int vg_stats(vg_grid *G, vg_stats_t *out) {
     out->points_in_grid = h[1];
     out->ray_visits = h[2];
     return VG_OK;
+}
+
+int vg_batch_create(int32_t capacity, vg_batch **out) {
+    if (!out) return VG_EINVAL;
+    *out = nullptr;
+    if (capacity < 1 || capacity > 65536) return VG_EINVAL;
+    vg_batch *B = new (std::nothrow) vg_batch();
+    if (!B) return VG_ENOMEM;
+    B->capacity = capacity;
+    B->bytes = sizeof(vg::BatchCtl) + (size_t)capacity * sizeof(vg::BatchItem);
+    cudaError_t e = cudaGetDevice(&B->device);
+    if (e == cudaSuccess) e = configure_device(B->device);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&B->dev, B->bytes);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&B->host, B->bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->copied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        vg_batch_destroy(B);
+        return status_of(e);
+    }
+    std::memset(B->host, 0, B->bytes);
+    *out = B;
+    return VG_OK;
+}
+
+void vg_batch_destroy(vg_batch *B) {
+    if (!B) return;
+    DeviceGuard dg(B->device);
+    cudaDeviceSynchronize();
+    if (B->copied) cudaEventDestroy(B->copied);
+    if (B->done) cudaEventDestroy(B->done);
+    cudaFreeHost(B->host);
+    cudaFree(B->dev);
+    delete B;
+}
+
+int vg_batch_tune(vg_batch *B, int32_t knob, int32_t value) {
+    if (!B) return VG_EINVAL;
+    if (knob == VG_TUNE_BATCH_CTAS_PER_SM) {
+        if (value < 0 || value > 64) return VG_EINVAL;
+        B->ctas_per_sm = value;
+        return VG_OK;
+    }
+    if (knob == VG_TUNE_BATCH_LANES) {
+        if (value != 0 && value != 8 && value != 16 && value != 32) return VG_EINVAL;
+        B->lanes = value;
+        return VG_OK;
+    }
+    return VG_EINVAL;
+}
+
+int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
+    if (!B || !frames || n < 1 || n > B->capacity) return VG_EINVAL;
+    // every frame's grid is distinct and usable, before any state changes
+    std::vector<const vg_grid *> seen;
+    seen.reserve((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        const vg_frame &f = frames[i];
+        const vg_grid *G = f.grid;
+        if (!G || !f.depth || f.width < 1 || f.height < 1) return VG_EINVAL;
+        if ((int64_t)f.width * f.height >= (int64_t(1) << 31)) return VG_EINVAL;
+        if (f.dtype != VG_DEPTH_F32 && f.dtype != VG_DEPTH_U16) return VG_EINVAL;
+        if (f.dtype == VG_DEPTH_U16 && !(std::isfinite(f.depth_scale) && f.depth_scale > 0.0f)) return VG_EINVAL;
+        if (G->device != B->device || G->p.vox_inf > 3) return VG_EINVAL;
+        if (f.recentre && !finite3(f.robot_pos_w)) return VG_EINVAL;
+        vg::Pose32 T;
+        if (!pose_of(G, f.T_wc, T)) return VG_EINVAL;
+        seen.push_back(G);
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return VG_EINVAL;
+
+    DeviceGuard dg(B->device);
+    if (!dg.ok) return VG_ECUDA;
+    if (B->enqueued) {
+        cudaError_t e = cudaEventSynchronize(B->copied);   // the table is free again
+        if (e != cudaSuccess) return status_of(e);
+    }
+    vg::BatchCtl *ctl = reinterpret_cast<vg::BatchCtl *>(B->host);
+    vg::BatchItem *items = reinterpret_cast<vg::BatchItem *>(B->host + sizeof(vg::BatchCtl));
+    int64_t total[5] = {0, 0, 0, 0, 0};
+    for (int32_t i = 0; i < n; ++i) {
+        const vg_frame &f = frames[i];
+        vg_grid *G = f.grid;
+        vg::Pose32 T;
+        pose_of(G, f.T_wc, T);
+        vg::BatchItem &it = items[i];
+        std::memset(&it, 0, sizeof(it));
+        it.a = depth_frame_args(G, T, f.depth, f.width, f.height, f.dtype, f.depth_scale);
+        if (G->p.vox_inf == 0) it.a.pl.occ_inf = it.a.pl.occ_raw;
+        it.dtype = f.dtype;
+        it.vec = (reinterpret_cast<uintptr_t>(f.depth) % (f.dtype == VG_DEPTH_F32 ? 16 : 8)) == 0;
+        int lpr = B->lanes ? B->lanes : (G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh));
+        it.lpr = lpr < 8 ? 8 : lpr;
+        it.txw = G->g.wx % 8 == 0 ? 8 : 4;
+        it.tiles[0] = (G->g.wx + it.txw - 1) / it.txw;
+        it.tiles[1] = (G->g.ny + 7) / 8;
+        it.tiles[2] = (G->g.nz + 7) / 8;
+        it.align8 = (G->g.nx % 8 == 0 && reinterpret_cast<uintptr_t>(G->loc) % 8 == 0) ? 1 : 0;
+        it.buffered = G->g.words < (int64_t(1) << 26) ? 1 : 0;
+        const int64_t npix = (int64_t)f.width * f.height;
+        const int64_t nrays = (2 * (int64_t)G->hw + 1) * (2 * (int64_t)G->hh + 1);
+        const int64_t units[5] = {
+            ((npix + 3) / 4 + 255) / 256,
+            G->p.vox_inf > 0 ? (int64_t)it.tiles[0] * it.tiles[1] * it.tiles[2] : 0,
+            (nrays + (256 / it.lpr) - 1) / (256 / it.lpr),
+            (G->g.words + 255) / 256,
+            0};
+        int64_t u5 = 0;
+        if (f.recentre) {
+            int32_t o2[3];
+            origin_of(&G->p, f.robot_pos_w, o2);
+            const int32_t d[3] = {o2[0] - G->origin[0], o2[1] - G->origin[1], o2[2] - G->origin[2]};
+            if (d[0] || d[1] || d[2]) {
+                it.dx = d[0];
+                it.dy = d[1];
+                it.dz = d[2];
+                it.loc_dst = G->loc_alt;
+                u5 = ((G->g.nvox + 15) / 16 + 255) / 256;
+                // host state after this step: the grid lives in loc_alt at o2
+                std::swap(G->loc, G->loc_alt);
+                std::memcpy(G->origin, o2, sizeof(o2));
+            }
+        }
+        for (int p = 0; p < 5; ++p) {
+            it.off[p] = total[p];
+            total[p] += (p == 4) ? u5 : units[p];
+        }
+        ++G->frames;
+    }
+    std::memset(ctl, 0, sizeof(*ctl));
+    ctl->n = n;
+    for (int p = 0; p < 5; ++p) ctl->total[p] = total[p];
+    B->bytes = sizeof(vg::BatchCtl) + (size_t)n * sizeof(vg::BatchItem);
+    B->prepared = true;
+    return VG_OK;
+}
+
+int vg_batch_enqueue(vg_batch *B, void *stream) {
+    if (!B || !B->prepared) return VG_EINVAL;
+    DeviceGuard dg(B->device);
+    if (!dg.ok) return VG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int max_blocks = vg::batch_max_blocks(B->device);
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device);
+    if (e != cudaSuccess) return status_of(e);
+    int blocks = max_blocks;
+    if (B->ctas_per_sm > 0 && B->ctas_per_sm * sms < max_blocks) blocks = B->ctas_per_sm * sms;
+    if (blocks < 1) return VG_ECUDA;
+    // under stream capture the events must become record nodes of the graph,
+    // so that every replay records them
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return status_of(e);
+    const unsigned rec = (cs == cudaStreamCaptureStatusActive) ? cudaEventRecordExternal : cudaEventRecordDefault;
+    e = cudaMemcpyAsync(B->dev, B->host, B->bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(B->copied, s, rec);
+    if (e == cudaSuccess)
+        e = vg::launch_batch(reinterpret_cast<const vg::BatchItem *>(B->dev + sizeof(vg::BatchCtl)),
+                             reinterpret_cast<vg::BatchCtl *>(B->dev), blocks, s);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(B->done, s, rec);
+    if (e != cudaSuccess) return status_of(e);
+    B->enqueued = true;
+    ++B->launches;
+    return VG_OK;
+}
+
+int vg_batch_step(vg_batch *B, const vg_frame *frames, int32_t n, void *stream) {
+    int rc = vg_batch_prepare(B, frames, n);
+    return rc == VG_OK ? vg_batch_enqueue(B, stream) : rc;
+}
+
+int vg_batch_status(vg_batch *B) {
+    if (!B) return VG_EINVAL;
+    if (!B->enqueued) return VG_OK;
+    DeviceGuard dg(B->device);
+    if (!dg.ok) return VG_ECUDA;
+    cudaError_t e = cudaEventSynchronize(B->done);
+    unsigned err = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&err, B->dev + offsetof(vg::BatchCtl, error), sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return status_of(e);
+    return err ? VG_ETIMEOUT : VG_OK;
+}
+
+int vg_batch_autotune(vg_batch *B, const vg_frame *frames, int32_t n, int32_t reps, void *stream,
+                      int32_t best[2]) {
+    if (!B || !frames || n < 1 || n > B->capacity || reps < 1) return VG_EINVAL;
+    std::vector<vg_frame> fr(frames, frames + n);
+    for (auto &f : fr) f.recentre = 0;
+    DeviceGuard dg(B->device);
+    if (!dg.ok) return VG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int max_blocks = vg::batch_max_blocks(B->device);
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device);
+    const int max_per_sm = std::max(1, max_blocks / std::max(1, sms));
+    cudaEvent_t t0, t1;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    if (e != cudaSuccess) return status_of(e);
+    const int lanes_c[4] = {0, 8, 16, 32};
+    float best_ms = 1e30f;
+    int best_c = 0, best_l = 0;
+    int rc = VG_OK;
+    for (int c = 1; c <= max_per_sm && rc == VG_OK; ++c) {
+        for (int li = 0; li < 4 && rc == VG_OK; ++li) {
+            B->ctas_per_sm = c;
+            B->lanes = lanes_c[li];
+            rc = vg_batch_step(B, fr.data(), n, stream);   // warm-up
+            if (rc != VG_OK) break;
+            e = cudaEventRecord(t0, s);
+            for (int r = 0; r < reps && rc == VG_OK && e == cudaSuccess; ++r) rc = vg_batch_step(B, fr.data(), n, stream);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e != cudaSuccess) rc = status_of(e);
+            if (rc == VG_OK) rc = vg_batch_status(B);
+            if (rc == VG_OK && ms < best_ms) {
+                best_ms = ms;
+                best_c = c;
+                best_l = lanes_c[li];
+            }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    B->ctas_per_sm = best_c;
+    B->lanes = best_l;
+    if (best) {
+        best[0] = best_c;
+        best[1] = best_l;
+    }
+    return rc;
 }
 
 }  // extern "C"

@@ -65,6 +65,38 @@ struct FrameArgs {
     unsigned long long *stats;  // NULL unless VG_FLAG_STATS
 };
 
+// One frame of a batch (k_batch.cu): its FrameArgs plus the layout of its
+// units in each phase.
+struct BatchItem {
+    FrameArgs a;
+    int64_t off[5];     // first unit of this frame in phases 1..5
+    int32_t tiles[3];   // inflate tile grid (x words / txw, y / 8, z / 8)
+    int32_t dtype;      // 0 f32, 1 u16
+    int32_t vec;        // depth base aligned for 4-pixel loads
+    int32_t lpr;        // K3 lanes per ray: 8, 16 or 32
+    int32_t txw;        // inflate tile width in words: 4 or 8
+    int32_t align8;     // loc rows and buffer allow 8-byte stores
+    int32_t buffered;   // packed visits fit (plane words < 2^26)
+    int32_t dx, dy, dz; // re-centre offset (phase 5)
+    uint8_t *loc_dst;   // re-centred grid (phase 5)
+};
+
+// Control block of a batch launch, copied to the device with the items.
+struct BatchCtl {
+    int32_t n;          // frames
+    int32_t pad0;
+    int64_t total[5];   // units per phase
+    unsigned bar_count; // grid barrier: arrivals
+    unsigned bar_gen;   // grid barrier: generation
+    unsigned error;     // set when a barrier wait ran out
+    unsigned pad1;
+};
+
+// How long a CTA waits at a grid barrier before giving up (clock64 cycles,
+// about four seconds at the GB300's SM clock; a phase of any batch that fits
+// the device ends far sooner).
+constexpr long long kBarrierCycles = 8000000000LL;
+
 inline __host__ __device__ int64_t plane_word(const PlaneGeom &g, int32_t x, int32_t y, int32_t z) {
     return ((int64_t)z * g.ny + y) * g.wx + (x >> 5);
 }
@@ -80,5 +112,8 @@ cudaError_t launch_raytrace(const FrameArgs &a, int lanes_per_ray, cudaStream_t 
 cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s);
 cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8_t *src,
                          uint8_t *dst, cudaStream_t s);
+cudaError_t configure_batch(int dev);   // once per device, before the first launch_batch
+int batch_max_blocks(int dev);          // CTAs of k_batch resident at once on the device
+cudaError_t launch_batch(const BatchItem *items, BatchCtl *ctl, int blocks, cudaStream_t s);
 
 }  // namespace vg

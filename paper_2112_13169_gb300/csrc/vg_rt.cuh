@@ -1,0 +1,461 @@
+// vg_rt.cuh -- K3, the free-space ray trace, as device functions over one
+// group of rays, shared by the one-kernel-per-step launch (k_raytrace.cu)
+// and the fused persistent launch (k_batch.cu).
+//
+//
+// Ray bundle: one ray per far-plane voxel (a, b, vox_depth) of the camera,
+// a in [-hw, hw], b in [-hh, hh]; ray id = (b + hh) * (2hw + 1) + (a + hw).
+// In voxel units the ray is the segment S + tau * D, tau in [0, 1], with
+//   S_k = t_k / vox_size,
+//   D_k = (R_k0 * a + R_k1 * b) + R_k2 * vox_depth.
+// The walk is Amanatides & Woo's: per active axis (D_k != 0 and 1/D_k
+// finite) the m-th face crossing happens at
+//   t_k(m) = ((float)(b0_k + step_k * m) - S_k) * (1 / D_k),
+//   b0_k = floor(S_k) + (D_k > 0),
+// always recomputed from the integer face; the next crossing is the smallest
+// t, the lowest axis on a tie; the walk ends at the first crossing >= 1.
+// The start voxel floor(S) is visited.  Voxels outside the grid are skipped.
+// 1/D_k is taken with the correctly rounded reciprocal, which is the IEEE
+// quotient 1/D_k; the face coordinate is kept as an exact float.
+//
+// Free-space rule (Alg. 2): voxels before the ray's first occupied voxel
+// (of the inflated plane) are marked free, voxels after it
+// unknown-and-traced; occupied voxels are never marked free.  The paper's
+// racy single-grid writes are replaced by two bit planes, fr and tr, merged
+// by K4 with precedence occupied > free > traced, so the result does not
+// depend on the order rays run in.
+//
+// Parallel walk.  LPR lanes of a warp share one ray.  Lane j owns the face
+// crossings with tau in [c_j, c_{j+1}), c_0 = -inf, c_LPR = 1, and the
+// other cuts split the part of the segment inside the grid evenly.  Because each axis's crossing times are non-decreasing in m,
+// the serial walk performs exactly the crossings with t < c_j before any
+// other, so lane j starts from voxel floor(S) + step * n(c_j), with
+// n_k(c) = #{m : t_k(m) < c} found by an estimate and an exact fix-up on
+// the same float expression, and then merges the three axes exactly as the
+// serial walk does.  The lanes' visit lists concatenate to the serial list.
+//
+// Pass 1: each lane walks its slice once and keeps its in-grid visits in
+// its own shared-memory column (kRtBuf entries), then finds the first
+// occupied one, kChunk occupancy words in flight at a time.  A ballot over
+// the ray's lanes gives the first lane F that met one.
+// Pass 2: each lane replays its visits and marks: lanes before F all free;
+// lane F free before its occupied voxel and traced after it; lanes after F
+// traced.  Marks after the first occupied voxel are written without
+// re-reading the occupancy: a traced mark on an occupied voxel is
+// overridden by K4.  Marks that fall in the same 32-voxel word are OR-ed in
+// a register and flushed with one atomicOr; near the camera, where all rays
+// overlap, they go to a per-CTA shared-memory box first (see kBoxW).
+// A lane whose slice holds more than kRtBuf in-grid visits, or a grid whose
+// planes are too large for a packed visit, walks twice instead.
+//
+// The CTAs are persistent: each loops over groups of kThreads / LPR rays,
+// so the box is staged and flushed once per CTA.
+#pragma once
+
+#include "vg_units.cuh"
+
+namespace vg {
+namespace rt {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kChunk = 4;   // occupancy words loaded together
+constexpr int kThreads = 256;
+
+// The box around the camera voxel: kBoxW plane words (x) by kBoxY rows by
+// kBoxZ slices.  Its occupancy words are staged in shared memory once per
+// CTA and its free/traced marks are OR-ed there, then flushed once per CTA.
+constexpr int kBoxW = 2, kBoxY = 16, kBoxZ = 16;
+constexpr int kBoxWords = kBoxW * kBoxY * kBoxZ;
+
+// A visit packed in 32 bits: bit 31 set -> box word (index in bits 5..),
+// else the plane bit index P = ((z*ny + y) * 32*wx + x) < 2^31; bits 0..4
+// are x & 31 either way, so p >> 5 is the word.
+constexpr uint32_t kBoxFlag = 0x80000000u;
+
+struct Box {
+    int32_t bw0, by0, bz0;
+};
+
+// Per-ray constants of one lane.
+struct Ray {
+    float S[3];      // start, voxel units
+    float inv[3];    // 1/D, 0 for an inactive axis
+    float fs[3];     // step as float
+    int32_t s[3];    // step: -1, 0, +1
+    int32_t dP[3];   // change of the plane bit index per step
+    int32_t nx, ny, nz;
+};
+
+struct Walker {
+    float t0, t1, t2;     // next crossing time per axis
+    float nb0, nb1, nb2;  // coordinate of the next face per axis (exact)
+    int32_t i0, i1, i2;   // voxel
+    uint32_t P;           // plane bit index, modulo 2^32 outside the grid
+};
+
+__device__ __forceinline__ float cross_at(float b, float S, float inv) {
+    return __fmul_rn(__fsub_rn(b, S), inv);
+}
+
+// Number of crossings of axis k with t < c (c finite, > 0).
+__device__ __forceinline__ int32_t crossings_before(const Ray &r, int k, float absD, float c) {
+    if (r.s[k] == 0) return 0;
+    const int32_t b0 = (int32_t)floorf(r.S[k]) + (r.s[k] > 0 ? 1 : 0);
+    const float t0 = cross_at((float)b0, r.S[k], r.inv[k]);
+    if (!(t0 < c)) return 0;
+    const float est = __fmul_rn(__fsub_rn(c, t0), absD);
+    int32_t m = est < 1.0e7f ? (int32_t)est + 1 : 10000000;
+    while (m > 1 && !(cross_at((float)(b0 + r.s[k] * (m - 1)), r.S[k], r.inv[k]) < c)) --m;
+    while (cross_at((float)(b0 + r.s[k] * m), r.S[k], r.inv[k]) < c) ++m;
+    return m;
+}
+
+__device__ __forceinline__ void walker_init(Walker &w, const Ray &r, const int32_t n0[3], uint32_t R) {
+    w.i0 = (int32_t)floorf(r.S[0]) + r.s[0] * n0[0];
+    w.i1 = (int32_t)floorf(r.S[1]) + r.s[1] * n0[1];
+    w.i2 = (int32_t)floorf(r.S[2]) + r.s[2] * n0[2];
+    w.nb0 = (float)(w.i0 + (r.s[0] > 0 ? 1 : 0));
+    w.nb1 = (float)(w.i1 + (r.s[1] > 0 ? 1 : 0));
+    w.nb2 = (float)(w.i2 + (r.s[2] > 0 ? 1 : 0));
+    w.t0 = r.s[0] ? cross_at(w.nb0, r.S[0], r.inv[0]) : INFINITY;
+    w.t1 = r.s[1] ? cross_at(w.nb1, r.S[1], r.inv[1]) : INFINITY;
+    w.t2 = r.s[2] ? cross_at(w.nb2, r.S[2], r.inv[2]) : INFINITY;
+    w.P = ((uint32_t)w.i2 * (uint32_t)r.ny + (uint32_t)w.i1) * R + (uint32_t)w.i0;
+}
+
+// Advances to the next voxel if the next crossing is before c_hi.  The axis
+// with the smallest tMax moves, the lowest axis on a tie: x iff t0 is the
+// minimum, else y iff t1 is, else z.  The three updates are short, mutually
+// exclusive blocks, so lanes stepping different axes do not diverge.
+__device__ __forceinline__ bool walker_next(Walker &w, const Ray &r, float c_hi) {
+    const float tm = fminf(w.t0, fminf(w.t1, w.t2));
+    if (!(tm < c_hi)) return false;
+    const bool mx = (w.t0 == tm);
+    const bool my = !mx && (w.t1 == tm);
+    const bool mz = !mx && !my;
+    if (mx) {
+        w.i0 += r.s[0];
+        w.P += (uint32_t)r.dP[0];
+        w.nb0 = __fadd_rn(w.nb0, r.fs[0]);
+        w.t0 = cross_at(w.nb0, r.S[0], r.inv[0]);
+    }
+    if (my) {
+        w.i1 += r.s[1];
+        w.P += (uint32_t)r.dP[1];
+        w.nb1 = __fadd_rn(w.nb1, r.fs[1]);
+        w.t1 = cross_at(w.nb1, r.S[1], r.inv[1]);
+    }
+    if (mz) {
+        w.i2 += r.s[2];
+        w.P += (uint32_t)r.dP[2];
+        w.nb2 = __fadd_rn(w.nb2, r.fs[2]);
+        w.t2 = cross_at(w.nb2, r.S[2], r.inv[2]);
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool in_grid(const Walker &w, const Ray &r) {
+    return (unsigned)w.i0 < (unsigned)r.nx && (unsigned)w.i1 < (unsigned)r.ny &&
+           (unsigned)w.i2 < (unsigned)r.nz;
+}
+
+// True when an out-of-grid axis can no longer come back.
+__device__ __forceinline__ bool gone(const Walker &w, const Ray &r) {
+    return (w.i0 < 0 && r.s[0] <= 0) || (w.i0 >= r.nx && r.s[0] >= 0) || (w.i1 < 0 && r.s[1] <= 0) ||
+           (w.i1 >= r.ny && r.s[1] >= 0) || (w.i2 < 0 && r.s[2] <= 0) || (w.i2 >= r.nz && r.s[2] >= 0);
+}
+
+__device__ __forceinline__ uint32_t pack_visit(const Walker &w, const Box &b) {
+    const uint32_t dw = (uint32_t)((w.i0 >> 5) - b.bw0), dy = (uint32_t)(w.i1 - b.by0),
+                   dz = (uint32_t)(w.i2 - b.bz0);
+    if (dw < kBoxW && dy < kBoxY && dz < kBoxZ)
+        return kBoxFlag | (((dz * kBoxY + dy) * kBoxW + dw) << 5) | ((uint32_t)w.i0 & 31u);
+    return w.P;
+}
+
+template <class L>
+__device__ __forceinline__ uint32_t occ_word(const FrameArgs &a, const uint32_t *occ_box, uint32_t p) {
+    return (p & kBoxFlag) ? occ_box[(p >> 5) & (kBoxWords - 1)] : L::ld(a.pl.occ_inf + (p >> 5));
+}
+
+// Pending marks of one lane: consecutive marks of the same word and kind
+// are OR-ed in a register; a change of word or kind flushes them, to the
+// shared box or to the plane.
+struct Marks {
+    uint32_t key = 0xffffffffu;   // p >> 5 of the pending word
+    uint32_t bits = 0;
+    bool traced = false;
+};
+
+__device__ __forceinline__ void marks_flush(const FrameArgs &a, uint32_t *box_fr, uint32_t *box_tr,
+                                            const Marks &m) {
+    if (!m.bits) return;
+    if (m.key & (kBoxFlag >> 5)) atomicOr((m.traced ? box_tr : box_fr) + (m.key & (kBoxWords - 1)), m.bits);
+    else atomicOr((m.traced ? a.pl.tr : a.pl.fr) + m.key, m.bits);
+}
+
+__device__ __forceinline__ void marks_add(const FrameArgs &a, uint32_t *box_fr, uint32_t *box_tr, Marks &m,
+                                          uint32_t p, bool traced) {
+    const uint32_t key = p >> 5;
+    if (key != m.key || traced != m.traced) {
+        marks_flush(a, box_fr, box_tr, m);
+        m.key = key;
+        m.traced = traced;
+        m.bits = 0;
+    }
+    m.bits |= 1u << (p & 31u);
+}
+
+// Two-pass walk for a lane whose slice does not fit its buffer: returns the
+// index (among the slice's in-grid visits) of the first occupied voxel, or -1.
+template <class L>
+__device__ int walk_first_hit(const FrameArgs &a, const Ray &r, const int32_t n0[3], bool visit_start,
+                              float c_hi, const Box &b, const uint32_t *occ_box, uint32_t R) {
+    Walker w;
+    walker_init(w, r, n0, R);
+    bool more = visit_start ? true : walker_next(w, r, c_hi);
+    int32_t q = 0;
+    while (more) {
+        uint32_t p[kChunk];
+        int n = 0;
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) {
+            p[c] = 0;
+            while (more && n == c) {
+                if (in_grid(w, r)) {
+                    p[c] = pack_visit(w, b);
+                    ++n;
+                } else if (gone(w, r)) {
+                    more = false;
+                    break;
+                }
+                more = walker_next(w, r, c_hi);
+            }
+        }
+        uint32_t v[kChunk];
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) v[c] = c < n ? occ_word<L>(a, occ_box, p[c]) : 0u;
+        int hit = -1;
+#pragma unroll
+        for (int c = kChunk - 1; c >= 0; --c)
+            if (c < n && ((v[c] >> (p[c] & 31u)) & 1u)) hit = c;
+        if (hit >= 0) return q + hit;
+        q += n;
+    }
+    return -1;
+}
+
+// Pass 2 of the two-pass walk: marks the slice's in-grid visits.
+__device__ inline unsigned walk_marks(const FrameArgs &a, const Ray &r, const int32_t n0[3], bool visit_start,
+                               float c_hi, const Box &b, int mode, int32_t hit_at, uint32_t *box_fr,
+                               uint32_t *box_tr, uint32_t R) {
+    Walker w;
+    walker_init(w, r, n0, R);
+    bool more = visit_start ? true : walker_next(w, r, c_hi);
+    int32_t q = 0;
+    Marks m;
+    while (more) {
+        if (in_grid(w, r)) {
+            // mode: 0 all free, 1 free before hit_at and traced after, 2 all traced
+            if (!(mode == 1 && q == hit_at))
+                marks_add(a, box_fr, box_tr, m, pack_visit(w, b), mode == 2 || (mode == 1 && q > hit_at));
+            ++q;
+        } else if (gone(w, r)) {
+            break;
+        }
+        more = walker_next(w, r, c_hi);
+    }
+    marks_flush(a, box_fr, box_tr, m);
+    return (unsigned)q;
+}
+
+// The camera box of this frame: its origin, then staging of its occupancy
+// words (zero outside the grid) and clearing of its marks.  CTA-cooperative;
+// ends with a barrier.
+__device__ __forceinline__ Box box_of(const float S[3]) {
+    Box b;
+    const int32_t cx0 = (int32_t)floorf(S[0]);
+    b.bw0 = (cx0 >> 5) - ((cx0 & 31) < 16 ? 1 : 0);   // x words bw0, bw0+1
+    b.by0 = (int32_t)floorf(S[1]) - kBoxY / 2;
+    b.bz0 = (int32_t)floorf(S[2]) - kBoxZ / 2;
+    return b;
+}
+
+template <class L>
+__device__ __forceinline__ void box_stage(const FrameArgs &a, const Box &b, uint32_t *box_fr, uint32_t *box_tr,
+                                          uint32_t *occ_box) {
+    for (int i = threadIdx.x; i < kBoxWords; i += kThreads) {
+        box_fr[i] = 0;
+        box_tr[i] = 0;
+        const int32_t dw = i % kBoxW, dy = (i / kBoxW) % kBoxY, dz = i / (kBoxW * kBoxY);
+        const int32_t wx = b.bw0 + dw, y = b.by0 + dy, z = b.bz0 + dz;
+        uint32_t v = 0;
+        if (wx >= 0 && wx < a.g.wx && y >= 0 && y < a.g.ny && z >= 0 && z < a.g.nz)
+            v = L::ld(a.pl.occ_inf + ((uint32_t)z * (uint32_t)a.g.ny + (uint32_t)y) * (uint32_t)a.g.wx + wx);
+        occ_box[i] = v;
+    }
+    __syncthreads();
+}
+
+// ORs the box's marks into the planes.  CTA-cooperative; starts with a
+// barrier so every lane's marks are in.
+__device__ __forceinline__ void box_flush(const FrameArgs &a, const Box &b, const uint32_t *box_fr,
+                                          const uint32_t *box_tr) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBoxWords; i += kThreads) {
+        const uint32_t f = box_fr[i], t = box_tr[i];
+        if ((f | t) == 0) continue;
+        const int32_t dw = i % kBoxW, dy = (i / kBoxW) % kBoxY, dz = i / (kBoxW * kBoxY);
+        // only in-grid voxels are ever marked, so the word exists
+        const uint32_t gw = ((uint32_t)(b.bz0 + dz) * (uint32_t)a.g.ny + (uint32_t)(b.by0 + dy)) *
+                                (uint32_t)a.g.wx + (uint32_t)(b.bw0 + dw);
+        if (f) atomicOr(a.pl.fr + gw, f);
+        if (t) atomicOr(a.pl.tr + gw, t);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void frame_start(const FrameArgs &a, float S[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) S[k] = __fdiv_rn(a.T.t[k], a.vs);
+}
+
+// One group of kThreads / LPR rays (group index `group`) of one frame, by
+// all threads of the CTA; `buf` is this CTA's visit buffer (kRtBuf columns of
+// kThreads words).  Returns this thread's in-grid visits.  Warp-synchronous
+// (every lane of every warp must call it; the CTA need not be in step).
+template <int LPR, class L>
+__device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3], const Box &b, int64_t group,
+                                             int buffered, uint32_t *box_fr, uint32_t *box_tr,
+                                             const uint32_t *occ_box, uint32_t *buf) {
+    const int lane = threadIdx.x & 31;
+    const int j = lane & (LPR - 1);
+    const int32_t width = 2 * a.hw + 1;
+    const int64_t nrays = (int64_t)width * (2 * a.hh + 1);
+    const uint32_t R = 32u * (uint32_t)a.g.wx;   // plane bits per row
+    const int rays_per_cta = kThreads / LPR;
+    const int64_t ray = group * rays_per_cta + threadIdx.x / LPR;
+    const bool active = ray < nrays;
+    unsigned visits = 0;
+    Ray r;
+    r.nx = a.g.nx;
+    r.ny = a.g.ny;
+    r.nz = a.g.nz;
+    float absD[3];
+    {
+        const int32_t ra = active ? (int32_t)(ray % width) - a.hw : 0;
+        const int32_t rb = active ? (int32_t)(ray / width) - a.hh : 0;
+        const float fa = (float)ra, fb = (float)rb, fvd = (float)a.vd;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float d = __fadd_rn(__fadd_rn(__fmul_rn(a.T.R[k * 3 + 0], fa),
+                                                __fmul_rn(a.T.R[k * 3 + 1], fb)),
+                                      __fmul_rn(a.T.R[k * 3 + 2], fvd));
+            absD[k] = fabsf(d);
+            r.S[k] = S[k];
+            r.inv[k] = 0.0f;
+            r.s[k] = 0;
+            if (d != 0.0f) {
+                const float q = __frcp_rn(d);
+                if (isfinite(q)) {
+                    r.inv[k] = q;
+                    r.s[k] = d > 0.0f ? 1 : -1;
+                }
+            }
+            r.fs[k] = (float)r.s[k];
+        }
+        r.dP[0] = r.s[0];
+        r.dP[1] = r.s[1] * (int32_t)R;
+        r.dP[2] = r.s[2] * (int32_t)R * a.g.ny;
+    }
+
+    // this lane's slice of tau: the in-grid part of the segment is cut
+    // into LPR equal pieces (any cuts give the same visits as long as
+    // neighbouring lanes agree on them and the last lane ends at 1)
+    float c_lo, c_hi;
+    {
+        float ts = 0.0f, te = 1.0f;
+        const float nk[3] = {(float)a.g.nx, (float)a.g.ny, (float)a.g.nz};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (r.s[k] != 0) {
+                const float t_lo = __fmul_rn(__fsub_rn(r.s[k] > 0 ? 0.0f : nk[k], S[k]), r.inv[k]);
+                const float t_hi = __fmul_rn(__fsub_rn(r.s[k] > 0 ? nk[k] : 0.0f, S[k]), r.inv[k]);
+                ts = fmaxf(ts, t_lo);
+                te = fminf(te, t_hi);
+            }
+        }
+        if (!(te > ts)) {
+            ts = 0.0f;
+            te = 1.0f;
+        }
+        const float span = __fsub_rn(te, ts);
+        c_lo = __fadd_rn(ts, __fmul_rn(span, (float)j / (float)LPR));
+        c_hi = (j == LPR - 1) ? 1.0f : __fadd_rn(ts, __fmul_rn(span, (float)(j + 1) / (float)LPR));
+    }
+    int32_t n0[3] = {0, 0, 0};
+    if (j > 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) n0[k] = crossings_before(r, k, absD[k], c_lo);
+    }
+
+    // ---- pass 1: walk the slice once, keep its in-grid visits --------
+    int32_t nvis = 0, hit_at = -1;
+    bool ovf = !buffered;
+    if (active && !ovf) {
+        Walker w;
+        walker_init(w, r, n0, R);
+        bool more = (j == 0) ? true : walker_next(w, r, c_hi);
+        while (more) {
+            if (in_grid(w, r)) {
+                if (nvis == kRtBuf) {
+                    ovf = true;
+                    break;
+                }
+                buf[nvis * kThreads + threadIdx.x] = pack_visit(w, b);
+                ++nvis;
+            } else if (gone(w, r)) {
+                break;
+            }
+            more = walker_next(w, r, c_hi);
+        }
+        // first occupied visit, kChunk occupancy words in flight at a time
+        for (int q0 = 0; !ovf && q0 < nvis && hit_at < 0; q0 += kChunk) {
+            uint32_t p[kChunk], v[kChunk];
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) p[c] = q0 + c < nvis ? buf[(q0 + c) * kThreads + threadIdx.x] : 0u;
+#pragma unroll
+            for (int c = 0; c < kChunk; ++c) v[c] = q0 + c < nvis ? occ_word<L>(a, occ_box, p[c]) : 0u;
+#pragma unroll
+            for (int c = kChunk - 1; c >= 0; --c)
+                if (q0 + c < nvis && ((v[c] >> (p[c] & 31u)) & 1u)) hit_at = q0 + c;
+        }
+    }
+    if (active && ovf) hit_at = walk_first_hit<L>(a, r, n0, j == 0, c_hi, b, occ_box, R);
+
+    // ---- first lane of this ray with an occupied voxel ---------------
+    const unsigned hits = __ballot_sync(kFull, hit_at >= 0);
+    const int gbase = lane & ~(LPR - 1);
+    const unsigned gmask = (LPR == 32) ? kFull : (((1u << LPR) - 1u) << gbase);
+    const unsigned gh = hits & gmask;
+    const int F = gh ? (__ffs(gh) - 1 - gbase) : LPR;
+    const int mode = j < F ? 0 : (j == F ? 1 : 2);
+
+    // ---- pass 2: mark free / traced -----------------------------------
+    if (active && !ovf) {
+        Marks m;
+        for (int q = 0; q < nvis; ++q) {
+            if (mode == 1 && q == hit_at) continue;
+            marks_add(a, box_fr, box_tr, m, buf[q * kThreads + threadIdx.x],
+                      mode == 2 || (mode == 1 && q > hit_at));
+        }
+        marks_flush(a, box_fr, box_tr, m);
+        visits += (unsigned)nvis;
+    } else if (active) {
+        visits += walk_marks(a, r, n0, j == 0, c_hi, b, mode, hit_at, box_fr, box_tr, R);
+    }
+    return visits;
+}
+
+}  // namespace rt
+}  // namespace vg

@@ -25,7 +25,10 @@ VG_FLAG_STATS = 1
 # every symbol include/vg.h declares
 EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points", "vg_shift",
            "vg_read", "vg_write", "vg_get_origin", "vg_grid_bytes", "vg_ray_bundle", "vg_stats",
-           "vg_profile_enable", "vg_profile_read", "vg_tune", "vg_strerror", "vg_integrate_depth_noalloc")
+           "vg_profile_enable", "vg_profile_read", "vg_tune", "vg_strerror", "vg_integrate_depth_noalloc",
+           "vg_batch_create", "vg_batch_destroy", "vg_batch_prepare", "vg_batch_enqueue", "vg_batch_step",
+           "vg_batch_status", "vg_batch_tune", "vg_batch_autotune")
+VG_TUNE_BATCH_CTAS_PER_SM, VG_TUNE_BATCH_LANES = 100, 101
 KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift")
 VG_TUNE_RT_LANES = 0
 
@@ -38,6 +41,12 @@ class vg_params(C.Structure):
 
 class vg_stats_t(C.Structure):
     _fields_ = [("frames", C.c_uint64), ("points_in_grid", C.c_uint64), ("ray_visits", C.c_uint64)]
+
+
+class vg_frame(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("depth", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32),
+                ("dtype", C.c_int32), ("depth_scale", C.c_float), ("T_wc", C.c_double * 16),
+                ("recentre", C.c_int32), ("pad", C.c_int32), ("robot_pos_w", C.c_double * 3)]
 
 
 class VGError(RuntimeError):
@@ -76,6 +85,14 @@ def load(path=None):
         "vg_tune": (C.c_int, [vp, i32, i32]),
         "vg_strerror": (C.c_char_p, [C.c_int]),
         "vg_integrate_depth_noalloc": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, f32, vp, vp]),
+        "vg_batch_create": (C.c_int, [i32, C.POINTER(vp)]),
+        "vg_batch_destroy": (None, [vp]),
+        "vg_batch_prepare": (C.c_int, [vp, vp, i32]),
+        "vg_batch_enqueue": (C.c_int, [vp, vp]),
+        "vg_batch_step": (C.c_int, [vp, vp, i32, vp]),
+        "vg_batch_status": (C.c_int, [vp]),
+        "vg_batch_tune": (C.c_int, [vp, i32, i32]),
+        "vg_batch_autotune": (C.c_int, [vp, vp, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -311,6 +328,79 @@ class Grid:
     def close(self):
         if self.h:
             vg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_frames(frames):
+    """ctypes array of vg_frame from (grid, depth, T_wc, recentre_pos_or_None[, depth_scale])
+    tuples; grid is a Grid, depth a CUDA tensor."""
+    arr = (vg_frame * len(frames))()
+    for i, f in enumerate(frames):
+        grid, depth, T_wc, pos = f[0], f[1], f[2], f[3]
+        scale = f[4] if len(f) > 4 else 1.0
+        ptr, mem, nbytes, dt = _buffer(depth)
+        if mem != VG_MEM_DEVICE:
+            raise ValueError("batched depth frames must be device buffers")
+        if dt not in ("float32", "uint16"):
+            raise ValueError("depth must be float32 or uint16, got " + dt)
+        H, W = depth.shape
+        fr = arr[i]
+        fr.grid = grid.h.value if isinstance(grid.h, C.c_void_p) else grid.h
+        fr.depth = ptr
+        fr.width, fr.height = int(W), int(H)
+        fr.dtype = VG_DEPTH_F32 if dt == "float32" else VG_DEPTH_U16
+        fr.depth_scale = float(scale)
+        T = np.asarray(T_wc, np.float64).reshape(16)
+        for k in range(16):
+            fr.T_wc[k] = float(T[k])
+        if pos is not None:
+            fr.recentre = 1
+            for k in range(3):
+                fr.robot_pos_w[k] = float(pos[k])
+    return arr
+
+
+class Batch:
+    """Many grids' measurements in one persistent fused launch (vg_batch_*)."""
+
+    def __init__(self, capacity):
+        self.h = C.c_void_p()
+        _check(load().vg_batch_create(int(capacity), C.byref(self.h)), "vg_batch_create")
+        self.capacity = int(capacity)
+
+    def prepare(self, frames):
+        arr = make_frames(frames)
+        _check(load().vg_batch_prepare(self.h, arr, len(frames)), "vg_batch_prepare")
+
+    def enqueue(self, stream=None):
+        _check(load().vg_batch_enqueue(self.h, _stream(stream)), "vg_batch_enqueue")
+
+    def step(self, frames, stream=None):
+        arr = make_frames(frames)
+        _check(load().vg_batch_step(self.h, arr, len(frames), _stream(stream)), "vg_batch_step")
+
+    def status(self):
+        return load().vg_batch_status(self.h)
+
+    def tune(self, knob, value):
+        _check(load().vg_batch_tune(self.h, int(knob), int(value)), "vg_batch_tune")
+
+    def autotune(self, frames, reps=3, stream=None):
+        arr = make_frames(frames)
+        best = (C.c_int32 * 2)()
+        _check(load().vg_batch_autotune(self.h, arr, len(frames), int(reps), _stream(stream), best),
+               "vg_batch_autotune")
+        return int(best[0]), int(best[1])
+
+    def close(self):
+        if self.h:
+            load().vg_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
