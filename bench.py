@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle sample budget")
     ap.add_argument("--preroll", type=float, default=1.0, help="seconds of untimed frames before timing")
+    ap.add_argument("--batch-robots", type=int, default=64, help="robots per step of the batched form (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the batched form")
     return ap.parse_args()
 
 
@@ -253,6 +255,144 @@ def raytrace_traffic():
     return None
 
 
+def _pcts(ms):
+    ms = np.asarray(ms, np.float64)
+    return {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)), "mean": float(ms.mean())}
+
+
+def measure_fused_seq(vg, w, args, flush, stream):
+    """The sequence workload through the fused launch, one frame per batch."""
+    import torch
+    g = w.grid
+    F = len(w.frames)
+    depth = [torch.from_numpy(f.depth).cuda() for f in w.frames]
+    grid = vg.Grid(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos)
+    batch = vg.Batch(1)
+    for k in range(max(3, args.warmup)):
+        f = w.frames[k % F]
+        batch.step([(grid, depth[k % F], f.T_wc, f.robot_pos, w.cam.scale)])
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        f = w.frames[k % F]
+        flush.zero_()
+        ev[k][0].record(stream)
+        batch.step([(grid, depth[k % F], f.T_wc, f.robot_pos, w.cam.scale)])
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    status = batch.status()
+    lat = [a.elapsed_time(b) for a, b in ev]
+    batch.close()
+    grid.close()
+    return {"form": "fused: one persistent launch per frame (batch of 1)", "status": vg.strerror(status),
+            "value": w.nvox * args.steps / (sum(lat) / 1e3) / 1e6, "unit": "Mvoxel-updates/s",
+            "latency_ms": _pcts(lat), "l2": "flushed before every step"}
+
+
+def measure_batched(vg, args, rank, stream):
+    """The multi-robot workload: every robot's frame of a step in one fused
+    launch (eager, and replayed from a CUDA graph), against the plain path
+    on the same frames."""
+    import torch
+    from synth import make
+    R = args.batch_robots
+    ws = [make("robot", robot=i + 1000 * rank, frames=8) for i in range(R)]
+    F = 8
+    depth = [[torch.from_numpy(f.depth).cuda() for f in w.frames] for w in ws]
+    nvox = sum(w.nvox for w in ws)
+
+    def grids():
+        return [vg.Grid(w.grid.n, w.grid.vox_size, w.cam.fov_x, w.cam.fov_y, w.grid.depth, w.grid.vox_inf,
+                        w.frames[0].robot_pos) for w in ws]
+
+    def frames_of(gs, k):
+        return [(gs[i], depth[i][k % F], w.frames[k % F].T_wc, w.frames[k % F].robot_pos, w.cam.scale)
+                for i, w in enumerate(ws)]
+
+    steps = args.batch_steps
+    out = {"workload": "%d robots per step, each its own seeded scene and trajectory; depth %s f32; voxel "
+                       "{0.05, 0.1, 0.2} m; grids 80..256 x 80..256 x 40..96; vox_inf 1-3; %.1f M voxels and "
+                       "%.0f MB of depth per step" % (R, "{320x240, 640x480, 848x480}", nvox / 1e6,
+                                                      sum(w.frames[0].depth.nbytes for w in ws) / 1e6),
+           "steps": steps, "l2": "inputs and grids (> 1 GB) exceed L2; no flush"}
+
+    # batched, eager
+    gb = grids()
+    batch = vg.Batch(R)
+    ctas, lanes = batch.autotune(frames_of(gb, 0), reps=2, stream=stream)
+    for k in range(3):
+        batch.step(frames_of(gb, k), stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = time.perf_counter()
+    for k in range(steps):
+        ev[k][0].record(stream)
+        batch.step(frames_of(gb, k), stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    lat = [a.elapsed_time(b) for a, b in ev]
+    out["batched"] = {"form": "one persistent fused launch per step", "status": vg.strerror(batch.status()),
+                      "value": nvox * steps / (sum(lat) / 1e3) / 1e6, "unit": "Mvoxel-updates/s",
+                      "step_ms": _pcts(lat), "per_frame_latency_ms": _pcts(lat),
+                      "host_wall_Mvoxel_updates_per_s": nvox * steps / wall / 1e6,
+                      "autotuned": {"ctas_per_sm": ctas, "lanes_per_ray": lanes or "per grid"}}
+
+    # batched, replayed from a CUDA graph (prepare on the host, replay)
+    batch.prepare(frames_of(gb, 0))
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            batch.enqueue(cap)
+    graph.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = time.perf_counter()
+    for k in range(steps):
+        batch.prepare(frames_of(gb, k + 1))
+        ev[k][0].record(stream)
+        graph.replay()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    lat = [a.elapsed_time(b) for a, b in ev]
+    out["batched_graph"] = {"form": "the fused launch replayed from a CUDA graph",
+                            "status": vg.strerror(batch.status()),
+                            "value": nvox * steps / (sum(lat) / 1e3) / 1e6, "unit": "Mvoxel-updates/s",
+                            "step_ms": _pcts(lat), "host_wall_Mvoxel_updates_per_s": nvox * steps / wall / 1e6}
+    del graph
+    batch.close()
+    for g in gb:
+        g.close()
+
+    # plain, the same frames one robot at a time
+    gp = grids()
+    for k in range(2):
+        for i, w in enumerate(ws):
+            f = w.frames[k % F]
+            gp[i].integrate_depth(depth[i][k % F], f.T_wc, w.cam.scale)
+            gp[i].shift(f.robot_pos)
+    torch.cuda.synchronize()
+    psteps = max(3, steps // 4)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(psteps)]
+    for k in range(psteps):
+        ev[k][0].record(stream)
+        for i, w in enumerate(ws):
+            f = w.frames[k % F]
+            gp[i].integrate_depth(depth[i][k % F], f.T_wc, w.cam.scale)
+            gp[i].shift(f.robot_pos)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    lat = [a.elapsed_time(b) for a, b in ev]
+    out["plain"] = {"form": "plain: five launches per frame, robot after robot", "steps": psteps,
+                    "value": nvox * psteps / (sum(lat) / 1e3) / 1e6, "unit": "Mvoxel-updates/s", "step_ms": _pcts(lat)}
+    for g in gp:
+        g.close()
+    out["speedup_batched_vs_plain"] = out["batched"]["value"] / out["plain"]["value"]
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2112_13169_gb300 import build as vgbuild
@@ -361,6 +501,12 @@ def run_ours(args):
     grid.close()
     e2e_value = dist.sum(w.nvox * args.steps) / dist.max(e2e_s) / 1e6
 
+    # ---- other forms (reported beside the headline) ------------------------
+    forms = {"fused_seq": measure_fused_seq(vg, w, args, flush, stream)}
+    if args.batch_robots > 0:
+        forms["multi_robot"] = measure_batched(vg, args, dist.rank, stream)
+    t_forms_end = time.time()
+
     if clocks:
         clocks.stop()
 
@@ -428,6 +574,7 @@ def run_ours(args):
         "clocks": {"sm_mhz": summ["sm_mhz"], "sm_max_mhz": summ["sm_max_mhz"], "reasons": summ["reasons"],
                    "samples": summ["samples"]},
         "wall_s_timed_region": t_wall1 - t_wall0,
+        "forms": forms,
     }
     print(json.dumps(line))
     dist.close()

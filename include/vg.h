@@ -278,6 +278,91 @@ VG_API int vg_batch_tune(vg_batch *batch, int32_t knob, int32_t value);
 VG_API int vg_batch_autotune(vg_batch *batch, const vg_frame *frames, int32_t n, int32_t reps,
                              void *stream, int32_t best[2]);
 
+/*
+ * Served form: a request loop for many cameras with continuous batching.
+ * A server owns one grid per admitted camera (all resident on the device),
+ * a pinned host pool for submitted frames and device staging for the frames
+ * of the launches in flight.  A server thread forms batches from the queued
+ * requests -- oldest first, at most one frame per camera per launch, so the
+ * frames of one camera apply in submission order -- copies their depth to
+ * the device on a copy stream while the previous launch computes, and runs
+ * each batch as one fused launch (as vg_batch_step).  Requests that arrive
+ * while launches are on the GPU join the next launch as soon as a launch
+ * slot frees up.  Every entry point is thread-safe.
+ *
+ *  memory_budget  bytes of device memory the server may hold: its staging
+ *                 and tables plus the grids of the cameras it admits.
+ *  max_batch      frames per launch (1 .. 4096).
+ *  max_width, max_height
+ *                 the largest depth frame a camera may submit.
+ *  queue_depth    launches on the GPU at once (1 .. 8); 2 overlaps the next
+ *                 launch's copies with the current launch.
+ *  pending_frames submitted frames the host pool holds (queued or in
+ *                 flight) before vg_server_submit reports VG_EBUSY.
+ */
+typedef struct {
+    int64_t memory_budget;
+    int32_t max_batch;
+    int32_t max_width, max_height;
+    int32_t queue_depth;
+    int32_t pending_frames;
+} vg_server_params;
+
+typedef struct {
+    uint64_t submitted, completed, failed, batches;
+    double mean_batch;        /* frames per launch */
+    double latency_p50_us;    /* submission to completion of the frame's launch */
+    double latency_p99_us;
+    double latency_max_us;
+    int64_t bytes_in_use;     /* device bytes held (staging, tables, grids) */
+    int32_t cameras;
+} vg_server_stats_t;
+
+typedef struct vg_server vg_server;
+
+/* Creates the server on the current device and starts its thread.
+ * Errors: VG_EINVAL, VG_ENOMEM (budget below the server's own needs or an
+ * allocation failed), VG_ECUDA. */
+VG_API int vg_server_create(const vg_server_params *params, vg_server **out);
+
+/* Finishes every queued frame, stops the thread and frees everything. */
+VG_API void vg_server_destroy(vg_server *server);
+
+/* Admits a camera with its own grid (see vg_create) if the memory budget
+ * allows; *camera receives its id.  Errors: VG_EINVAL, VG_ENOMEM (over
+ * budget or out of memory), VG_ECUDA. */
+VG_API int vg_server_add_camera(vg_server *server, const vg_params *params, const double robot_pos_w[3],
+                                int32_t *camera);
+
+/* Waits for the camera's queued frames, then frees its grid and returns its
+ * memory to the budget.  Errors: VG_EINVAL. */
+VG_API int vg_server_remove_camera(vg_server *server, int32_t camera);
+
+/*
+ * Queues one frame of a camera: depth is host memory (W x H, dtype as for
+ * vg_integrate_depth) and is copied into the server's pool before the call
+ * returns.  recentre != 0 re-centres the grid on robot_pos_w after the
+ * merge.  *ticket (may be NULL) identifies the request.
+ * Errors: VG_EINVAL (bad argument, frame larger than max_width x max_height,
+ * unknown or removed camera), VG_EBUSY (the pool is full: retry later).
+ */
+VG_API int vg_server_submit(vg_server *server, int32_t camera, const void *depth, int32_t width,
+                            int32_t height, int32_t dtype, float depth_scale, const double T_wc[16],
+                            int32_t recentre, const double robot_pos_w[3], uint64_t *ticket);
+
+/* Waits up to timeout_us microseconds (negative: no limit) for a request.
+ * Returns VG_OK when its launch completed, VG_ETIMEOUT if still pending,
+ * VG_ECUDA or VG_EINVAL if it failed or is unknown. */
+VG_API int vg_server_wait(vg_server *server, uint64_t ticket, int64_t timeout_us);
+
+/* Waits for every queued frame of the camera, then copies its grid to dst
+ * (as vg_read) and synchronises.  Errors: VG_EINVAL, VG_ECUDA. */
+VG_API int vg_server_read(vg_server *server, int32_t camera, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes,
+                          int32_t origin[3]);
+
+/* Counters and latency percentiles since creation or the last reset. */
+VG_API int vg_server_stats(vg_server *server, vg_server_stats_t *out, int32_t reset);
+
 /* Kernels of one measurement, for profiling and launch counts. */
 enum {
     VG_K_VOXELIZE = 0, /* K1 */

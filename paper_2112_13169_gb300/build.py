@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvg.so")
 
 SOURCES = ["vg_api.cu", "k_voxelize.cu", "k_inflate.cu", "k_raytrace.cu", "k_merge.cu", "k_batch.cu",
-           "vg_noalloc.cu"]
+           "vg_noalloc.cu", "vg_server.cu"]
 NO_FMAD = {"k_voxelize.cu", "k_raytrace.cu", "k_batch.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,0 +1,440 @@
+// vg_server.cu -- the served form: continuous batching of measurements from
+// many cameras (declared in include/vg.h).
+//
+// Client threads submit frames (copied into a pinned host pool) into one
+// arrival-ordered queue.  The server thread repeatedly
+//   - finishes launches whose completion callback fired (status, latencies,
+//     freeing their pool slots and launch slot),
+//   - forms a batch when a launch slot is free: the oldest queued frames,
+//     at most one per camera, skipping cameras being read,
+//   - copies the batch's depth frames to device staging on the copy stream,
+//     makes the compute stream wait for the copies, and runs the batch as one
+//     fused launch (vg_batch_prepare + vg_batch_enqueue) on the compute stream,
+//     followed by a host callback that stamps the completion time.
+// With queue_depth >= 2 the copies of the next launch overlap the current
+// launch, and frames arriving meanwhile join the next launch.  Frames of one
+// camera apply in submission order: one per launch, launches in stream order.
+//
+// The mutex is never held across a CUDA call that could wait for the host
+// callback (the callback takes the mutex and makes no CUDA call), and the
+// server's streams are non-blocking so a synchronous copy elsewhere does not
+// wait for them.
+#include "vg.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket;
+    int32_t camera, slot, width, height, dtype, recentre;
+    float scale;
+    double T_wc[16], pos[3];
+    Clock::time_point arrival;
+};
+
+struct Camera {
+    vg_grid *grid = nullptr;
+    int64_t bytes = 0;
+    bool removed = false;
+    bool reading = false;
+    int32_t pending = 0;   // queued or in flight
+};
+
+struct Launch {
+    vg_server *srv = nullptr;
+    vg_batch *batch = nullptr;
+    uint8_t *staging = nullptr;   // max_batch frames of device staging
+    cudaEvent_t copied = nullptr;
+    std::vector<Request> reqs;
+    bool busy = false;
+    bool gpu_done = false;
+    Clock::time_point done_at;
+};
+
+}  // namespace
+
+struct vg_server {
+    vg_server_params p;
+    int device = 0;
+    size_t frame_bytes = 0;
+    cudaStream_t compute = nullptr, copy = nullptr, admin = nullptr;
+    uint8_t *pinned = nullptr;
+    std::vector<int32_t> free_slots;
+    std::vector<Camera> cams;
+    std::deque<Request> queue;
+    std::vector<Launch> launches;
+    int32_t inflight = 0;
+    int64_t fixed_bytes = 0, grid_bytes = 0;
+    std::vector<uint8_t> status;   // per ticket: 0 pending, 1 done, 2 failed
+    uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_frames = 0;
+    std::vector<float> lat_us;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread th;
+    bool stop = false;
+};
+
+namespace {
+
+void CUDART_CB on_launch_done(void *arg) {
+    Launch *L = static_cast<Launch *>(arg);
+    vg_server *S = L->srv;
+    std::lock_guard<std::mutex> g(S->mu);
+    L->gpu_done = true;
+    L->done_at = Clock::now();
+    S->cv.notify_all();
+}
+
+bool any_done(const vg_server *S) {
+    for (const Launch &L : S->launches)
+        if (L.busy && L.gpu_done) return true;
+    return false;
+}
+
+bool can_launch(const vg_server *S) {
+    if (S->inflight >= S->p.queue_depth) return false;
+    for (const Request &r : S->queue)
+        if (!S->cams[r.camera].reading) return true;
+    return false;
+}
+
+// Under the lock: retire a launch whose work ended with status st.
+void finish(vg_server *S, Launch &L, int st, Clock::time_point when) {
+    for (const Request &r : L.reqs) {
+        S->status[r.ticket] = st == VG_OK ? 1 : 2;
+        if (st == VG_OK) {
+            ++S->completed;
+            S->lat_us.push_back((float)std::chrono::duration<double, std::micro>(when - r.arrival).count());
+        } else {
+            ++S->failed;
+        }
+        --S->cams[r.camera].pending;
+        S->free_slots.push_back(r.slot);
+    }
+    ++S->batches;
+    S->batched_frames += L.reqs.size();
+    L.reqs.clear();
+    L.busy = false;
+    L.gpu_done = false;
+    --S->inflight;
+    S->cv.notify_all();
+}
+
+// Issues one formed batch; returns its status (VG_OK once enqueued).
+int issue(vg_server *S, Launch &L) {
+    const size_t n = L.reqs.size();
+    for (size_t k = 0; k < n; ++k) {
+        const Request &r = L.reqs[k];
+        const size_t bytes = (size_t)r.width * r.height * (r.dtype == VG_DEPTH_F32 ? 4 : 2);
+        cudaError_t e = cudaMemcpyAsync(L.staging + k * S->frame_bytes, S->pinned + (size_t)r.slot * S->frame_bytes,
+                                        bytes, cudaMemcpyHostToDevice, S->copy);
+        if (e != cudaSuccess) return VG_ECUDA;
+    }
+    if (cudaEventRecord(L.copied, S->copy) != cudaSuccess) return VG_ECUDA;
+    if (cudaStreamWaitEvent(S->compute, L.copied, 0) != cudaSuccess) return VG_ECUDA;
+    std::vector<vg_frame> fr(n);
+    for (size_t k = 0; k < n; ++k) {
+        const Request &r = L.reqs[k];
+        vg_frame &f = fr[k];
+        std::memset(&f, 0, sizeof(f));
+        f.grid = S->cams[r.camera].grid;
+        f.depth = L.staging + k * S->frame_bytes;
+        f.width = r.width;
+        f.height = r.height;
+        f.dtype = r.dtype;
+        f.depth_scale = r.scale;
+        std::memcpy(f.T_wc, r.T_wc, sizeof(f.T_wc));
+        f.recentre = r.recentre;
+        std::memcpy(f.robot_pos_w, r.pos, sizeof(f.robot_pos_w));
+    }
+    int rc = vg_batch_prepare(L.batch, fr.data(), (int32_t)n);
+    if (rc == VG_OK) rc = vg_batch_enqueue(L.batch, S->compute);
+    if (rc == VG_OK && cudaLaunchHostFunc(S->compute, on_launch_done, &L) != cudaSuccess) rc = VG_ECUDA;
+    return rc;
+}
+
+void server_loop(vg_server *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        std::vector<Launch *> done;
+        Launch *next = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] {
+                return any_done(S) || can_launch(S) || (S->stop && S->queue.empty() && S->inflight == 0);
+            });
+            for (Launch &L : S->launches)
+                if (L.busy && L.gpu_done) done.push_back(&L);
+            if (done.empty() && S->stop && S->queue.empty() && S->inflight == 0) return;
+            if (can_launch(S)) {
+                for (Launch &L : S->launches)
+                    if (!L.busy) {
+                        next = &L;
+                        break;
+                    }
+                // the oldest frames, at most one per camera, none of a camera being read
+                std::vector<char> used(S->cams.size(), 0);
+                for (auto it = S->queue.begin();
+                     it != S->queue.end() && next->reqs.size() < (size_t)S->p.max_batch;) {
+                    if (used[it->camera] || S->cams[it->camera].reading) {
+                        ++it;
+                        continue;
+                    }
+                    used[it->camera] = 1;
+                    next->reqs.push_back(*it);
+                    it = S->queue.erase(it);
+                }
+                next->busy = true;
+                next->gpu_done = false;
+                ++S->inflight;
+            }
+        }
+        for (Launch *L : done) {
+            const int st = vg_batch_status(L->batch);   // the launch has ended; no wait
+            std::lock_guard<std::mutex> g(S->mu);
+            finish(S, *L, st, L->done_at);
+        }
+        if (next) {
+            const int rc = issue(S, *next);
+            if (rc != VG_OK) {
+                // nothing of this batch reaches the callback: finish it here,
+                // once the copies that did start have ended
+                cudaStreamSynchronize(S->copy);
+                std::lock_guard<std::mutex> g(S->mu);
+                finish(S, *next, rc, Clock::now());
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int vg_server_create(const vg_server_params *p, vg_server **out) {
+    if (!out) return VG_EINVAL;
+    *out = nullptr;
+    if (!p || p->max_batch < 1 || p->max_batch > 4096 || p->queue_depth < 1 || p->queue_depth > 8 ||
+        p->max_width < 1 || p->max_height < 1 || (int64_t)p->max_width * p->max_height >= (int64_t(1) << 31) ||
+        p->pending_frames < p->max_batch || p->memory_budget <= 0)
+        return VG_EINVAL;
+    vg_server *S = new (std::nothrow) vg_server();
+    if (!S) return VG_ENOMEM;
+    S->p = *p;
+    S->frame_bytes = ((size_t)p->max_width * p->max_height * 4 + 255) & ~size_t(255);
+    const size_t staging = S->frame_bytes * (size_t)p->max_batch;
+    // staging and a generous bound on each launch's descriptor table
+    S->fixed_bytes = (int64_t)(staging + (size_t)p->max_batch * 1024 + 4096) * p->queue_depth;
+    if (S->fixed_bytes > p->memory_budget) {
+        delete S;
+        return VG_ENOMEM;
+    }
+    cudaError_t e = cudaGetDevice(&S->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->admin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&S->pinned, S->frame_bytes * (size_t)p->pending_frames);
+    int rc = e == cudaSuccess ? VG_OK : (e == cudaErrorMemoryAllocation ? VG_ENOMEM : VG_ECUDA);
+    S->launches.resize((size_t)p->queue_depth);
+    for (Launch &L : S->launches) {
+        if (rc != VG_OK) break;
+        L.srv = S;
+        rc = vg_batch_create(p->max_batch, &L.batch);
+        if (rc == VG_OK && cudaMalloc((void **)&L.staging, staging) != cudaSuccess) rc = VG_ENOMEM;
+        if (rc == VG_OK && cudaEventCreateWithFlags(&L.copied, cudaEventDisableTiming) != cudaSuccess) rc = VG_ECUDA;
+    }
+    if (rc != VG_OK) {
+        vg_server_destroy(S);
+        return rc;
+    }
+    for (int32_t i = p->pending_frames - 1; i >= 0; --i) S->free_slots.push_back(i);
+    try {
+        S->th = std::thread(server_loop, S);
+    } catch (...) {
+        vg_server_destroy(S);
+        return VG_ENOMEM;
+    }
+    *out = S;
+    return VG_OK;
+}
+
+void vg_server_destroy(vg_server *S) {
+    if (!S) return;
+    if (S->th.joinable()) {
+        {
+            std::lock_guard<std::mutex> g(S->mu);
+            S->stop = true;
+            S->cv.notify_all();
+        }
+        S->th.join();
+    }
+    cudaSetDevice(S->device);
+    if (S->compute) cudaStreamSynchronize(S->compute);
+    if (S->copy) cudaStreamSynchronize(S->copy);
+    for (Launch &L : S->launches) {
+        vg_batch_destroy(L.batch);
+        cudaFree(L.staging);
+        if (L.copied) cudaEventDestroy(L.copied);
+    }
+    for (Camera &c : S->cams)
+        if (c.grid) vg_destroy(c.grid);
+    cudaFreeHost(S->pinned);
+    if (S->compute) cudaStreamDestroy(S->compute);
+    if (S->copy) cudaStreamDestroy(S->copy);
+    if (S->admin) cudaStreamDestroy(S->admin);
+    delete S;
+}
+
+int vg_server_add_camera(vg_server *S, const vg_params *params, const double robot_pos_w[3], int32_t *camera) {
+    if (!S || !params || !robot_pos_w || !camera || params->vox_inf > 3) return VG_EINVAL;
+    const int64_t bytes = vg_grid_bytes(params);
+    if (bytes <= 0) return VG_EINVAL;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (S->fixed_bytes + S->grid_bytes + bytes > S->p.memory_budget) return VG_ENOMEM;
+        S->grid_bytes += bytes;   // reserved while the grid is made
+    }
+    vg_grid *grid = nullptr;
+    int rc = vg_create(params, robot_pos_w, S->admin, &grid);
+    std::lock_guard<std::mutex> g(S->mu);
+    if (rc != VG_OK) {
+        S->grid_bytes -= bytes;
+        return rc;
+    }
+    Camera c;
+    c.grid = grid;
+    c.bytes = bytes;
+    S->cams.push_back(c);
+    *camera = (int32_t)S->cams.size() - 1;
+    return VG_OK;
+}
+
+int vg_server_remove_camera(vg_server *S, int32_t camera) {
+    if (!S) return VG_EINVAL;
+    vg_grid *grid = nullptr;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (camera < 0 || camera >= (int32_t)S->cams.size() || S->cams[camera].removed) return VG_EINVAL;
+        S->cams[camera].removed = true;
+        S->cv.wait(lk, [&] { return S->cams[camera].pending == 0; });
+        grid = S->cams[camera].grid;
+        S->cams[camera].grid = nullptr;
+        S->grid_bytes -= S->cams[camera].bytes;
+    }
+    vg_destroy(grid);
+    return VG_OK;
+}
+
+int vg_server_submit(vg_server *S, int32_t camera, const void *depth, int32_t width, int32_t height, int32_t dtype,
+                     float depth_scale, const double T_wc[16], int32_t recentre, const double robot_pos_w[3],
+                     uint64_t *ticket) {
+    const Clock::time_point arrival = Clock::now();
+    if (!S || !depth || !T_wc || width < 1 || height < 1 || width > S->p.max_width || height > S->p.max_height)
+        return VG_EINVAL;
+    if (dtype != VG_DEPTH_F32 && dtype != VG_DEPTH_U16) return VG_EINVAL;
+    if (dtype == VG_DEPTH_U16 && !(depth_scale > 0.0f && depth_scale < 1e30f)) return VG_EINVAL;
+    if (recentre && !robot_pos_w) return VG_EINVAL;
+    for (int i = 0; i < 16; ++i)
+        if (!(T_wc[i] == T_wc[i]) || T_wc[i] > 1e300 || T_wc[i] < -1e300) return VG_EINVAL;
+    Request r;
+    r.camera = camera;
+    r.width = width;
+    r.height = height;
+    r.dtype = dtype;
+    r.scale = depth_scale;
+    r.recentre = recentre != 0;
+    std::memcpy(r.T_wc, T_wc, sizeof(r.T_wc));
+    if (recentre) std::memcpy(r.pos, robot_pos_w, sizeof(r.pos));
+    else std::memset(r.pos, 0, sizeof(r.pos));
+    r.arrival = arrival;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (camera < 0 || camera >= (int32_t)S->cams.size() || S->cams[camera].removed) return VG_EINVAL;
+        if (S->free_slots.empty()) return VG_EBUSY;
+        r.slot = S->free_slots.back();
+        S->free_slots.pop_back();
+        ++S->cams[camera].pending;   // keeps the camera alive while the frame is copied in
+    }
+    const size_t bytes = (size_t)width * height * (dtype == VG_DEPTH_F32 ? 4 : 2);
+    std::memcpy(S->pinned + (size_t)r.slot * S->frame_bytes, depth, bytes);
+    std::lock_guard<std::mutex> g(S->mu);
+    r.ticket = S->status.size();
+    S->status.push_back(0);
+    ++S->submitted;
+    S->queue.push_back(r);
+    if (ticket) *ticket = r.ticket;
+    S->cv.notify_all();
+    return VG_OK;
+}
+
+int vg_server_wait(vg_server *S, uint64_t ticket, int64_t timeout_us) {
+    if (!S) return VG_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (ticket >= S->status.size()) return VG_EINVAL;
+    auto ready = [&] { return S->status[ticket] != 0; };
+    if (timeout_us < 0) S->cv.wait(lk, ready);
+    else if (!S->cv.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) return VG_ETIMEOUT;
+    return S->status[ticket] == 1 ? VG_OK : VG_ECUDA;
+}
+
+int vg_server_read(vg_server *S, int32_t camera, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes,
+                   int32_t origin[3]) {
+    if (!S) return VG_EINVAL;
+    vg_grid *grid = nullptr;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (camera < 0 || camera >= (int32_t)S->cams.size() || S->cams[camera].removed) return VG_EINVAL;
+        S->cv.wait(lk, [&] { return S->cams[camera].pending == 0 && !S->cams[camera].reading; });
+        S->cams[camera].reading = true;   // the server leaves the grid alone meanwhile
+        grid = S->cams[camera].grid;
+    }
+    int rc = vg_read(grid, dst, dst_mem, dst_bytes, origin, S->admin);
+    if (rc == VG_OK && cudaStreamSynchronize(S->admin) != cudaSuccess) rc = VG_ECUDA;
+    std::lock_guard<std::mutex> g(S->mu);
+    S->cams[camera].reading = false;
+    S->cv.notify_all();
+    return rc;
+}
+
+int vg_server_stats(vg_server *S, vg_server_stats_t *out, int32_t reset) {
+    if (!S || !out) return VG_EINVAL;
+    std::lock_guard<std::mutex> g(S->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = S->submitted;
+    out->completed = S->completed;
+    out->failed = S->failed;
+    out->batches = S->batches;
+    out->mean_batch = S->batches ? (double)S->batched_frames / (double)S->batches : 0.0;
+    if (!S->lat_us.empty()) {
+        std::vector<float> v(S->lat_us);
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return (double)v[std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5))]; };
+        out->latency_p50_us = pct(0.50);
+        out->latency_p99_us = pct(0.99);
+        out->latency_max_us = v.back();
+    }
+    out->bytes_in_use = S->fixed_bytes + S->grid_bytes;
+    int32_t live = 0;
+    for (const Camera &c : S->cams) live += c.removed ? 0 : 1;
+    out->cameras = live;
+    if (reset) {
+        S->submitted = S->completed = S->failed = S->batches = S->batched_frames = 0;
+        S->lat_us.clear();
+    }
+    return VG_OK;
+}
+
+}  // extern "C"

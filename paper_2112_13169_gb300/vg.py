@@ -27,7 +27,9 @@ EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points
            "vg_read", "vg_write", "vg_get_origin", "vg_grid_bytes", "vg_ray_bundle", "vg_stats",
            "vg_profile_enable", "vg_profile_read", "vg_tune", "vg_strerror", "vg_integrate_depth_noalloc",
            "vg_batch_create", "vg_batch_destroy", "vg_batch_prepare", "vg_batch_enqueue", "vg_batch_step",
-           "vg_batch_status", "vg_batch_tune", "vg_batch_autotune")
+           "vg_batch_status", "vg_batch_tune", "vg_batch_autotune", "vg_server_create", "vg_server_destroy",
+           "vg_server_add_camera", "vg_server_remove_camera", "vg_server_submit", "vg_server_wait",
+           "vg_server_read", "vg_server_stats")
 VG_TUNE_BATCH_CTAS_PER_SM, VG_TUNE_BATCH_LANES = 100, 101
 KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift")
 VG_TUNE_RT_LANES = 0
@@ -47,6 +49,18 @@ class vg_frame(C.Structure):
     _fields_ = [("grid", C.c_void_p), ("depth", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32),
                 ("dtype", C.c_int32), ("depth_scale", C.c_float), ("T_wc", C.c_double * 16),
                 ("recentre", C.c_int32), ("pad", C.c_int32), ("robot_pos_w", C.c_double * 3)]
+
+
+class vg_server_params(C.Structure):
+    _fields_ = [("memory_budget", C.c_int64), ("max_batch", C.c_int32), ("max_width", C.c_int32),
+                ("max_height", C.c_int32), ("queue_depth", C.c_int32), ("pending_frames", C.c_int32)]
+
+
+class vg_server_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("batches", C.c_uint64), ("mean_batch", C.c_double), ("latency_p50_us", C.c_double),
+                ("latency_p99_us", C.c_double), ("latency_max_us", C.c_double), ("bytes_in_use", C.c_int64),
+                ("cameras", C.c_int32)]
 
 
 class VGError(RuntimeError):
@@ -93,6 +107,14 @@ def load(path=None):
         "vg_batch_status": (C.c_int, [vp]),
         "vg_batch_tune": (C.c_int, [vp, i32, i32]),
         "vg_batch_autotune": (C.c_int, [vp, vp, i32, i32, vp, vp]),
+        "vg_server_create": (C.c_int, [vp, C.POINTER(vp)]),
+        "vg_server_destroy": (None, [vp]),
+        "vg_server_add_camera": (C.c_int, [vp, vp, vp, vp]),
+        "vg_server_remove_camera": (C.c_int, [vp, i32]),
+        "vg_server_submit": (C.c_int, [vp, i32, vp, i32, i32, i32, f32, vp, i32, vp, vp]),
+        "vg_server_wait": (C.c_int, [vp, C.c_uint64, i64]),
+        "vg_server_read": (C.c_int, [vp, i32, vp, i32, i64, vp]),
+        "vg_server_stats": (C.c_int, [vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -401,6 +423,78 @@ class Batch:
     def close(self):
         if self.h:
             load().vg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop over many cameras (vg_server_*)."""
+
+    def __init__(self, memory_budget, max_batch=64, max_width=1280, max_height=720, queue_depth=2,
+                 pending_frames=None):
+        p = vg_server_params()
+        p.memory_budget = int(memory_budget)
+        p.max_batch = int(max_batch)
+        p.max_width = int(max_width)
+        p.max_height = int(max_height)
+        p.queue_depth = int(queue_depth)
+        p.pending_frames = int(pending_frames or 4 * max_batch)
+        self.h = C.c_void_p()
+        _check(load().vg_server_create(C.byref(p), C.byref(self.h)), "vg_server_create")
+
+    def add_camera(self, n, vox_size, fov_x_deg, fov_y_deg, depth, vox_inf, robot_pos_w=(0, 0, 0)):
+        params = make_params(n, vox_size, fov_x_deg, fov_y_deg, depth, vox_inf)
+        cam = C.c_int32()
+        pos, pp = _f64(robot_pos_w, 3)
+        _check(load().vg_server_add_camera(self.h, C.byref(params), pp, C.byref(cam)), "vg_server_add_camera")
+        return int(cam.value)
+
+    def remove_camera(self, camera):
+        _check(load().vg_server_remove_camera(self.h, int(camera)), "vg_server_remove_camera")
+
+    def submit(self, camera, depth, T_wc, robot_pos_w=None, depth_scale=1.0):
+        """Queue a host depth frame; returns its ticket, or None when the
+        server's pool is full (VG_EBUSY)."""
+        ptr, mem, nbytes, dt = _buffer(depth)
+        if mem != VG_MEM_HOST:
+            raise ValueError("served frames come from host memory")
+        dtype = VG_DEPTH_F32 if dt == "float32" else VG_DEPTH_U16 if dt == "uint16" else None
+        if dtype is None:
+            raise ValueError("depth must be float32 or uint16, got " + dt)
+        H, W = depth.shape
+        T, tp = _f64(T_wc, 16)
+        pos, pp = _f64(robot_pos_w if robot_pos_w is not None else (0, 0, 0), 3)
+        t = C.c_uint64()
+        rc = load().vg_server_submit(self.h, int(camera), C.c_void_p(ptr), int(W), int(H), dtype,
+                                     float(depth_scale), tp, 1 if robot_pos_w is not None else 0, pp, C.byref(t))
+        if rc == VG_EBUSY:
+            return None
+        _check(rc, "vg_server_submit")
+        return int(t.value)
+
+    def wait(self, ticket, timeout_us=-1):
+        return load().vg_server_wait(self.h, C.c_uint64(ticket), int(timeout_us))
+
+    def read(self, camera, dst):
+        ptr, mem, nbytes, _ = _buffer(dst)
+        o = np.zeros(3, np.int32)
+        _check(load().vg_server_read(self.h, int(camera), C.c_void_p(ptr), mem, nbytes,
+                                     o.ctypes.data_as(C.c_void_p)), "vg_server_read")
+        return o
+
+    def stats(self, reset=False):
+        st = vg_server_stats_t()
+        _check(load().vg_server_stats(self.h, C.byref(st), 1 if reset else 0), "vg_server_stats")
+        return {f[0]: getattr(st, f[0]) for f in st._fields_}
+
+    def close(self):
+        if self.h:
+            load().vg_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
