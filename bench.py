@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--preroll", type=float, default=1.0, help="seconds of untimed frames before timing")
     ap.add_argument("--batch-robots", type=int, default=64, help="robots per step of the batched form (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the batched form")
+    ap.add_argument("--serve-cameras", type=int, default=256, help="cameras of the served form (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="seconds of Poisson arrivals")
+    ap.add_argument("--serve-rate", type=float, default=30.0, help="frames per second per camera")
     return ap.parse_args()
 
 
@@ -393,6 +396,158 @@ def measure_batched(vg, args, rank, stream):
     return out
 
 
+def _arrivals(n_cams, rate, seconds, seed):
+    """Merged Poisson arrivals of n_cams cameras at `rate` Hz each: (time,
+    camera) pairs, time in seconds from the start."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    lam = n_cams * rate
+    while True:
+        t += rng.exponential(1.0 / lam)
+        if t > seconds:
+            return out
+        out.append((t, int(rng.integers(n_cams))))
+
+
+def measure_served(vg, args, rank):
+    """Simulated cameras with Poisson arrivals through the continuous-batching
+    server, and through a naive one-frame-at-a-time server for comparison."""
+    import queue
+    import threading
+    import torch
+    from synth import make
+    nseq = 16
+    seqs = [make("camera", robot=i + 100 * rank, frames=4) for i in range(nseq)]
+    n_req = args.serve_cameras
+    budget = 40 << 30
+    out = {"workload": "%d cameras, Poisson arrivals at %.0f Hz each for %.1f s; depth from {320x240 f32, "
+                       "640x480 f32, 640x480 u16, 1280x720 u16} with grids 80x80x40 at 0.1 m, 200x200x100 at "
+                       "0.05 m or 400x400x120 at 0.05 m (each camera draws one of %d rendered sequences and "
+                       "cycles its 4 frames); %d GB budget" % (n_req, args.serve_rate, args.serve_seconds, nseq,
+                                                               budget >> 30)}
+    # ---- continuous batching ---------------------------------------------
+    server = vg.Server(budget, max_batch=128, max_width=1280, max_height=720, queue_depth=2, pending_frames=1024)
+    cams = []
+    for i in range(n_req):
+        w = seqs[i % nseq]
+        g = w.grid
+        try:
+            cams.append((server.add_camera(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf,
+                                           w.frames[0].robot_pos), w))
+        except vg.VGError as e:
+            if e.status != vg.VG_ENOMEM:
+                raise
+            break
+    nc = len(cams)
+    warm = [server.submit(c, w.frames[0].depth, w.frames[0].T_wc, w.frames[0].robot_pos, w.cam.scale)
+            for c, w in cams]
+    for t in warm:
+        if t is not None:
+            server.wait(t)
+    server.stats(reset=True)
+    arr = _arrivals(nc, args.serve_rate, args.serve_seconds, 99 + rank)
+    nclient = 4
+    tickets = [[] for _ in range(nclient)]
+    late = [0.0] * nclient
+    counter = [1] * nc
+
+    # frames of one camera must be submitted in order: give each camera to one client
+    per_client = [[] for _ in range(nclient)]
+    for t, c in arr:
+        per_client[c % nclient].append((t, c))
+    arr = None
+    start = [time.perf_counter()]
+
+    def client_of(k):
+        t0 = start[0]
+        for t, c in per_client[k]:
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            late[k] = max(late[k], time.perf_counter() - t0 - t)
+            cid, w = cams[c]
+            f = w.frames[counter[c] % len(w.frames)]
+            counter[c] += 1
+            while True:
+                tk = server.submit(cid, f.depth, f.T_wc, f.robot_pos, w.cam.scale)
+                if tk is not None:
+                    tickets[k].append((tk, w.nvox))
+                    break
+                time.sleep(0.0002)
+
+    threads = [threading.Thread(target=client_of, args=(k,)) for k in range(nclient)]
+    start[0] = time.perf_counter()
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    ok = all(server.wait(tk) == vg.VG_OK for lst in tickets for tk, _ in lst)
+    elapsed = time.perf_counter() - start[0]
+    st = server.stats()
+    vox = sum(n for lst in tickets for _, n in lst)
+    out["served"] = {"form": "continuous batching: fused launches of up to 128 frames, 2 in flight",
+                     "cameras_admitted": nc, "all_ok": ok, "frames": int(st["completed"]),
+                     "frames_per_s": st["completed"] / elapsed, "value": vox / elapsed / 1e6,
+                     "unit": "Mvoxel-updates/s",
+                     "latency_ms": {"p50": st["latency_p50_us"] / 1e3, "p99": st["latency_p99_us"] / 1e3,
+                                    "max": st["latency_max_us"] / 1e3},
+                     "mean_frames_per_launch": st["mean_batch"], "launches": int(st["batches"]),
+                     "device_bytes_in_use": int(st["bytes_in_use"]),
+                     "client_max_lateness_ms": 1e3 * max(late)}
+    server.close()
+
+    # ---- a queue alone: one frame at a time through the plain path ---------
+    grids = []
+    for c, (cid, w) in enumerate(cams):
+        g = w.grid
+        grids.append(vg.Grid(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos))
+    q = queue.Queue()
+    lat = []
+    done = [0, 0]
+    stream = torch.cuda.current_stream()
+
+    def worker():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            t_arr, c = item
+            cid, w = cams[c]
+            f = w.frames[counter[c] % len(w.frames)]
+            counter[c] += 1
+            grids[c].integrate_depth(f.depth, f.T_wc, w.cam.scale)   # host depth: staged by the library
+            grids[c].shift(f.robot_pos)
+            stream.synchronize()
+            lat.append(time.perf_counter() - t_arr)
+            done[0] += 1
+            done[1] += w.nvox
+
+    wt = threading.Thread(target=worker)
+    wt.start()
+    arr2 = _arrivals(nc, args.serve_rate, args.serve_seconds, 99 + rank)
+    t0 = time.perf_counter()
+    for t, c in arr2:
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        q.put((t0 + t, c))
+    backlog = q.qsize()
+    q.put(None)
+    wt.join()
+    elapsed = time.perf_counter() - t0
+    for g in grids:
+        g.close()
+    lat_ms = np.asarray(lat) * 1e3
+    out["plain_queue"] = {"form": "a queue alone: one frame at a time, plain path, synchronised per frame",
+                          "frames": done[0], "frames_per_s": done[0] / elapsed, "value": done[1] / elapsed / 1e6,
+                          "unit": "Mvoxel-updates/s", "backlog_when_arrivals_stopped": backlog,
+                          "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                                         "p99": float(np.percentile(lat_ms, 99)), "max": float(lat_ms.max())}}
+    out["speedup_served_vs_plain_queue_p99_latency"] = (out["plain_queue"]["latency_ms"]["p99"] /
+                                                       max(1e-9, out["served"]["latency_ms"]["p99"]))
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2112_13169_gb300 import build as vgbuild
@@ -505,6 +660,8 @@ def run_ours(args):
     forms = {"fused_seq": measure_fused_seq(vg, w, args, flush, stream)}
     if args.batch_robots > 0:
         forms["multi_robot"] = measure_batched(vg, args, dist.rank, stream)
+    if args.serve_cameras > 0:
+        forms["served"] = measure_served(vg, args, dist.rank)
     t_forms_end = time.time()
 
     if clocks:

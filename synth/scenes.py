@@ -17,6 +17,9 @@ configurations of the project:
             primitives, 15% invalid; 400x400x120 at 0.05 m, vox_inf 2
   robot  -- one robot of the batched mix: resolution, voxel size, grid and
             vox_inf drawn from the stated sets
+  camera -- one camera of the served mix: 320x240 f32, 640x480 f32 or u16,
+            or 1280x720 u16, with a grid of 80x80x40 at 0.1 m, 200x200x100
+            at 0.05 m or 400x400x120 at 0.05 m
 
 Seeds are recipe_id * 1000 + robot index.  Nothing here computes any step
 of the voxel-grid method; the same frames feed the CPU oracle and the CUDA
@@ -277,4 +280,20 @@ def make(name, frames=None, seed=None, robot=0):
         grid = GridSpec(n, vs, 5.0, int(rng.integers(1, 4)))
         return _sequence(name, s, cam, grid, [0, 0, 0], [16, 16, 4], 120, [BOX, SPHERE, CYL],
                          frames or 8, 0.05, 0.005)
+    if name == "camera":
+        # one simulated camera of the served mix: resolution and pixel type
+        # from the stated set, the grid sized to the camera's range
+        s = 5000 + robot if seed is None else seed
+        rng = np.random.default_rng(s)
+        kind = int(rng.integers(4))
+        if kind == 0:
+            cam, grid = Camera(320, 240, 87.0, 58.0), GridSpec((80, 80, 40), 0.1, 4.0, 1)
+        elif kind == 1:
+            cam, grid = Camera(640, 480, 87.0, 58.0), GridSpec((200, 200, 100), 0.05, 5.0, 2)
+        elif kind == 2:
+            cam, grid = Camera(640, 480, 87.0, 58.0, "u16", 0.001), GridSpec((200, 200, 100), 0.05, 5.0, 2)
+        else:
+            cam, grid = Camera(1280, 720, 90.0, 60.0, "u16", 0.001), GridSpec((400, 400, 120), 0.05, 6.0, 2)
+        return _sequence(name, s, cam, grid, [0, 0, 0], [20, 20, 5], 150, [BOX, SPHERE, CYL], frames or 4,
+                         0.08, 0.005)
     raise ValueError("unknown workload " + name)
