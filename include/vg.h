@@ -116,7 +116,8 @@ typedef struct {
  * robot_pos_w (world metres) sits in voxel floor(N/2) of every axis:
  * origin_k = floor(p_k / vox_size) - floor(N_k / 2), computed in double.
  * Synchronises `stream` once before returning.
- * Errors: VG_EINVAL (NULL, out-of-range parameter), VG_ENOMEM, VG_ECUDA.
+ * Errors: VG_EINVAL (NULL, out-of-range parameter, robot_pos_w not finite or
+ * |robot_pos_w| / vox_size >= 2^30 on an axis), VG_ENOMEM, VG_ECUDA.
  */
 VG_API int vg_create(const vg_params *params, const double robot_pos_w[3], void *stream,
               vg_grid **out);
@@ -157,8 +158,13 @@ VG_API int vg_integrate_points(vg_grid *grid, const float *xyz, int32_t mem, int
 /*
  * Re-centre the grid on the robot (Sec. IV-E): the new origin o' is computed
  * as in vg_create; with delta = o' - o, loc'[i] = loc[i + delta] where that
- * voxel exists, else VG_UNK.  No device work when delta is zero.
- * Errors: VG_EINVAL, VG_ECUDA.
+ * voxel exists, else VG_UNK.  The origin changes at once (vg_get_origin);
+ * the copy of loc is deferred: the grid's next merge (vg_integrate_*, or a
+ * batch step) writes the re-centred grid whole as it merges, and vg_read or
+ * another vg_shift first applies a deferred re-centre on its own stream.
+ * No device work here unless a re-centre was already pending.
+ * Errors: VG_EINVAL (also: |robot_pos_w| / vox_size >= 2^30 on an axis),
+ * VG_ECUDA.
  */
 VG_API int vg_shift(vg_grid *grid, const double robot_pos_w[3], void *stream);
 
@@ -167,7 +173,8 @@ VG_API int vg_shift(vg_grid *grid, const double robot_pos_w[3], void *stream);
  * dst is valid once that work completes.  dst_mem is VG_MEM_DEVICE or
  * VG_MEM_HOST; dst_bytes must be >= Nx*Ny*Nz.  origin (may be NULL)
  * receives the grid origin (voxel index of voxel (0,0,0) in the world
- * lattice) as of this call.
+ * lattice) as of this call.  A pending re-centre (vg_shift) is applied on
+ * stream first.
  * Errors: VG_EINVAL, VG_ECUDA.
  */
 VG_API int vg_read(vg_grid *grid, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes,
@@ -176,7 +183,7 @@ VG_API int vg_read(vg_grid *grid, uint8_t *dst, int32_t dst_mem, int64_t dst_byt
 /*
  * Restore loc_grid and its origin (checkpoint / resume): src holds
  * Nx*Ny*Nz bytes of voxel codes 0..3 (not checked), src_bytes must equal
- * Nx*Ny*Nz.  Errors: VG_EINVAL, VG_ECUDA.
+ * Nx*Ny*Nz.  A pending re-centre is dropped.  Errors: VG_EINVAL, VG_ECUDA.
  */
 VG_API int vg_write(vg_grid *grid, const uint8_t *src, int32_t src_mem, int64_t src_bytes,
              const int32_t origin[3], void *stream);
@@ -229,8 +236,9 @@ VG_API void vg_batch_destroy(vg_batch *batch);
 /*
  * Host-only half of a step: validates the n frames and writes their
  * descriptors into the batch's pinned table, and applies the grids'
- * host-side state changes (origin and buffer swap of every re-centred
- * grid).  Waits for the previous step's table copy, so the table can be
+ * host-side state changes: a grid's pending re-centre is taken into this
+ * step's merge, and a frame's own re-centre is left pending on its grid
+ * (origin updated), as vg_shift leaves it.  Waits for the previous step's table copy, so the table can be
  * rewritten.  Grids must have vox_inf <= 3 and live on the batch's device.
  * Errors: VG_EINVAL (bad frame, two frames for one grid, n > capacity),
  * VG_ECUDA.
@@ -239,9 +247,9 @@ VG_API int vg_batch_prepare(vg_batch *batch, const vg_frame *frames, int32_t n);
 
 /*
  * Device half of a step: copies the table to the device and launches the
- * fused kernel on `stream` (cooperative launch: K1, K2, K3, K4 and the
- * re-centre of every prepared frame, with a grid-wide barrier between
- * phases).  Can be captured in a CUDA graph; replaying the graph runs
+ * fused kernel on `stream` (cooperative launch: K1, K2, K3 and K4 of
+ * every prepared frame, the merge applying each grid's pending re-centre,
+ * with a grid-wide barrier between phases).  Can be captured in a CUDA graph; replaying the graph runs
  * whatever vg_batch_prepare wrote last.  Errors: VG_EINVAL, VG_ECUDA.
  */
 VG_API int vg_batch_enqueue(vg_batch *batch, void *stream);

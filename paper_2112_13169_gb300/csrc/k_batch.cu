@@ -6,8 +6,9 @@
 //   phase 2  K2 inflate            8 x 8 x 8-word tiles (radius 1..3)
 //   phase 3  K3 ray trace          groups of 256 / LPR rays
 //   phase 4  K4 merge              256 plane words
-//   phase 5  K5 re-centre          4096 voxels (frames that shift only)
-// with a grid-wide barrier between phases.  Units of every frame are laid
+// with a grid-wide barrier between phases.  A frame's re-centre (K5) is not
+// a phase: it is left pending on its grid and applied by that grid's next
+// merge, which then writes the whole grid out of place (merge_shift_word).  Units of every frame are laid
 // end to end per phase (BatchItem::off), so a CTA picks a unit, finds its
 // frame by binary search and runs the same device code as the one-step
 // kernels (vg_units.cuh, vg_rt.cuh).  Reads of data an earlier phase wrote
@@ -26,6 +27,7 @@ using namespace rt;
 
 constexpr int kDynWords = kRtBuf * kThreads;   // also covers an inflate tile of radius <= 3
 static_assert(units::inflate_smem_words<3, 8, 8, 8>(3) <= (size_t)kDynWords, "inflate tile fits");
+static_assert(units::kMergeShiftSmem <= 4 * kDynWords, "merge-with-shift staging fits");
 
 __device__ __forceinline__ int find_item(const BatchItem *items, int n, int phase, int64_t u) {
     int lo = 0, hi = n - 1;
@@ -81,7 +83,7 @@ __device__ __forceinline__ unsigned group_lpr(const BatchItem &it, const float S
 
 __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restrict__ items, BatchCtl *ctl) {
     __shared__ uint32_t box_fr[kBoxWords], box_tr[kBoxWords], occ_box[kBoxWords];
-    extern __shared__ uint32_t dyn[];
+    extern __shared__ __align__(16) uint32_t dyn[];
     const int n = ctl->n;
     const unsigned nb = gridDim.x;
 
@@ -165,18 +167,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
         const int i = find_item(items, n, 3, u);
         const BatchItem &it = items[i];
         const int64_t w = (u - it.off[3]) * kThreads + threadIdx.x;
-        if (it.align8) units::merge_word<true, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
+        if (it.loc_dst)
+            units::merge_shift_unit<units::LoadL2, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, it.loc_dst, it.dx, it.dy, it.dz,
+                                                   u - it.off[3], reinterpret_cast<uint8_t *>(dyn));
+        else if (it.align8) units::merge_word<true, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
         else units::merge_word<false, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
-    }
-    if (ctl->total[4] == 0) return;
-    if (!grid_sync(ctl, nb)) return;
-
-    // ---- phase 5: re-centre -----------------------------------------------
-    for (int64_t u = blockIdx.x; u < ctl->total[4]; u += nb) {
-        const int i = find_item(items, n, 4, u);
-        const BatchItem &it = items[i];
-        const int64_t c = (u - it.off[4]) * kThreads + threadIdx.x;
-        units::shift_chunk<units::LoadL2>(it.a.g, it.dx, it.dy, it.dz, it.a.loc, it.loc_dst, c);
     }
 }
 

@@ -10,6 +10,8 @@ template <int R, int TXW, int TY, int TZ>
 __global__ void __launch_bounds__(256) k_inflate(const PlaneGeom g, const uint32_t *__restrict__ raw,
                                                  uint32_t *__restrict__ out, const int r_rt) {
     extern __shared__ uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
     units::inflate_tile<R, TXW, TY, TZ, units::LoadRO>(g, raw, out, r_rt, blockIdx.x, blockIdx.y, blockIdx.z, sm);
 }
 
@@ -17,8 +19,8 @@ template <int R, int TXW, int TY, int TZ>
 cudaError_t run(const FrameArgs &a, cudaStream_t s) {
     dim3 grid((a.g.wx + TXW - 1) / TXW, (a.g.ny + TY - 1) / TY, (a.g.nz + TZ - 1) / TZ);
     const size_t bytes = sizeof(uint32_t) * units::inflate_smem_words<R, TXW, TY, TZ>(a.r);
-    k_inflate<R, TXW, TY, TZ><<<grid, 256, bytes, s>>>(a.g, a.pl.occ_raw, a.pl.occ_inf, a.r);
-    return cudaGetLastError();
+    return launch_pdl(k_inflate<R, TXW, TY, TZ>, grid, 256, bytes, s, a.g, (const uint32_t *)a.pl.occ_raw,
+                      a.pl.occ_inf, a.r);
 }
 
 template <int TXW>

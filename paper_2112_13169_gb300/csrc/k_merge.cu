@@ -1,6 +1,6 @@
-// K4 (merge) and K5 (shift) as their own launches: one thread per plane word
-// and one thread per 16 bytes of the new grid; the work itself is in
-// vg_units.cuh.
+// K4 (merge), K4 with a pending re-centre, and K5 (shift) as their own
+// launches: one thread per plane word, one CTA per 256 plane words, or one
+// thread per 16 bytes of the new grid; the work itself is in vg_units.cuh.
 #include "vg_units.cuh"
 
 namespace vg {
@@ -8,12 +8,25 @@ namespace {
 
 template <bool ALIGN8>
 __global__ void __launch_bounds__(256) k_merge(const PlaneGeom g, Planes pl, uint8_t *__restrict__ loc) {
+    pdl_trigger();
+    pdl_wait();
     units::merge_word<ALIGN8, units::LoadPlain>(g, pl, loc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_merge_shift(const PlaneGeom g, Planes pl, const uint8_t *__restrict__ src,
+                                                     uint8_t *__restrict__ dst, const int32_t dx, const int32_t dy,
+                                                     const int32_t dz) {
+    __shared__ __align__(16) uint8_t sm[units::kMergeShiftSmem];
+    pdl_trigger();
+    pdl_wait();
+    units::merge_shift_unit<units::LoadRO, units::LoadPlain>(g, pl, src, dst, dx, dy, dz, blockIdx.x, sm);
 }
 
 __global__ void __launch_bounds__(256) k_shift(const PlaneGeom g, const int32_t dx, const int32_t dy,
                                                const int32_t dz, const uint8_t *__restrict__ src,
                                                uint8_t *__restrict__ dst) {
+    pdl_trigger();
+    pdl_wait();
     units::shift_chunk<units::LoadRO>(g, dx, dy, dz, src, dst, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -24,10 +37,15 @@ cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s) {
     if (blocks == 0) return cudaSuccess;
     // 8-byte loc stores need 8-byte aligned rows and buffer
     if (a.g.nx % 8 == 0 && reinterpret_cast<uintptr_t>(a.loc) % 8 == 0)
-        k_merge<true><<<blocks, 256, 0, s>>>(a.g, a.pl, a.loc);
-    else
-        k_merge<false><<<blocks, 256, 0, s>>>(a.g, a.pl, a.loc);
-    return cudaGetLastError();
+        return launch_pdl(k_merge<true>, blocks, 256, 0, s, a.g, a.pl, a.loc);
+    return launch_pdl(k_merge<false>, blocks, 256, 0, s, a.g, a.pl, a.loc);
+}
+
+cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s) {
+    const unsigned blocks = (unsigned)units::merge_shift_units(a.g);
+    if (blocks == 0) return cudaSuccess;
+    return launch_pdl(k_merge_shift, blocks, 256, 0, s, a.g, a.pl, (const uint8_t *)a.loc, dst, delta[0], delta[1],
+                      delta[2]);
 }
 
 cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8_t *src, uint8_t *dst,
@@ -35,8 +53,7 @@ cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8
     const int64_t threads = (g.nvox + 15) / 16;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     if (blocks == 0) return cudaSuccess;
-    k_shift<<<blocks, 256, 0, s>>>(g, delta[0], delta[1], delta[2], src, dst);
-    return cudaGetLastError();
+    return launch_pdl(k_shift, blocks, 256, 0, s, g, delta[0], delta[1], delta[2], src, dst);
 }
 
 }  // namespace vg

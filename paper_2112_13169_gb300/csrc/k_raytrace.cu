@@ -9,17 +9,24 @@ namespace {
 using namespace rt;
 
 template <int LPR>
-__global__ void __launch_bounds__(kThreads) k_raytrace(const FrameArgs a, const int buffered) {
+__global__ void __launch_bounds__(kThreads, 5) k_raytrace(const FrameArgs a, const int buffered) {
     __shared__ uint32_t box_fr[kBoxWords], box_tr[kBoxWords], occ_box[kBoxWords];
     extern __shared__ uint32_t buf[];   // kRtBuf * kThreads, one column per thread
+    pdl_trigger();
     float S[3];
     frame_start(a, S);
     const Box b = box_of(S);
-    box_stage<units::LoadRO>(a, b, box_fr, box_tr, occ_box);
     const int64_t nrays = (2 * (int64_t)a.hw + 1) * (2 * (int64_t)a.hh + 1);
     const int64_t groups = (nrays + (kThreads / LPR) - 1) / (kThreads / LPR);
-    unsigned visits = 0;
-    for (int64_t grp = blockIdx.x; grp < groups; grp += gridDim.x)
+    // the first group's set-up needs only the pose, so it overlaps the
+    // end of K2; the occupancy is read after the wait (every CTA has a
+    // first group: the grid is no larger than the group count)
+    Lane ln;
+    rt_setup<LPR>(a, S, blockIdx.x, ln);
+    pdl_wait();
+    box_stage<units::LoadRO>(a, b, box_fr, box_tr, occ_box);
+    unsigned visits = rt_walk<LPR, units::LoadRO>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
+    for (int64_t grp = blockIdx.x + gridDim.x; grp < groups; grp += gridDim.x)
         visits += rt_group<LPR, units::LoadRO>(a, S, b, grp, buffered, box_fr, box_tr, occ_box, buf);
     box_flush(a, b, box_fr, box_tr);
     if (a.stats) {
@@ -52,8 +59,7 @@ cudaError_t launch_lpr(const FrameArgs &a, int idx, cudaStream_t s) {
     if (blocks == 0) return cudaSuccess;
     // a packed visit holds a plane bit index below 2^31
     const int buffered = a.g.words < (int64_t(1) << 26) ? 1 : 0;
-    k_raytrace<LPR><<<blocks, kThreads, sizeof(uint32_t) * kRtBuf * kThreads, s>>>(a, buffered);
-    return cudaGetLastError();
+    return launch_pdl(k_raytrace<LPR>, blocks, kThreads, sizeof(uint32_t) * kRtBuf * kThreads, s, a, buffered);
 }
 
 }  // namespace

@@ -7,10 +7,14 @@ namespace {
 
 template <int DT, bool VEC>
 __global__ void __launch_bounds__(256) k_voxelize_depth(const FrameArgs a) {
+    pdl_trigger();
+    pdl_wait();   // the depth image and the planes belong to earlier work
     units::voxelize_depth_thread<DT, VEC>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_voxelize_points(const FrameArgs a) {
+    pdl_trigger();
+    pdl_wait();
     units::voxelize_points_thread(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -23,20 +27,17 @@ cudaError_t launch_voxelize_depth(const FrameArgs &a, int32_t dtype, cudaStream_
     if (blocks == 0) return cudaSuccess;
     const uintptr_t base = reinterpret_cast<uintptr_t>(a.depth);
     if (dtype == 0) {
-        if (base % 16 == 0) k_voxelize_depth<0, true><<<blocks, 256, 0, s>>>(a);
-        else k_voxelize_depth<0, false><<<blocks, 256, 0, s>>>(a);
-    } else {
-        if (base % 8 == 0) k_voxelize_depth<1, true><<<blocks, 256, 0, s>>>(a);
-        else k_voxelize_depth<1, false><<<blocks, 256, 0, s>>>(a);
+        if (base % 16 == 0) return launch_pdl(k_voxelize_depth<0, true>, blocks, 256, 0, s, a);
+        return launch_pdl(k_voxelize_depth<0, false>, blocks, 256, 0, s, a);
     }
-    return cudaGetLastError();
+    if (base % 8 == 0) return launch_pdl(k_voxelize_depth<1, true>, blocks, 256, 0, s, a);
+    return launch_pdl(k_voxelize_depth<1, false>, blocks, 256, 0, s, a);
 }
 
 cudaError_t launch_voxelize_points(const FrameArgs &a, cudaStream_t s) {
     const unsigned blocks = (unsigned)((a.npts + 255) / 256);
     if (blocks == 0) return cudaSuccess;
-    k_voxelize_points<<<blocks, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_voxelize_points, blocks, 256, 0, s, a);
 }
 
 }  // namespace vg

@@ -36,6 +36,12 @@ struct vg_grid {
     uint8_t *base;        // the one device allocation
     uint8_t *loc;
     uint8_t *loc_alt;
+    // A re-centre not yet applied to loc: the grid's content is loc shifted
+    // by pend (loc'[i] = loc[i + pend]); origin already holds o'.  The next
+    // merge applies it while it writes the grid out of place, so a frame
+    // followed by a re-centre costs one pass over loc instead of two.
+    bool pend_on;
+    int32_t pend[3];
     vg::Planes pl;
     unsigned long long *stats;
     void *staging;        // device copy of host inputs
@@ -78,6 +84,14 @@ double half_fov(float deg) { return (double)deg * kPi / 360.0; }
 
 bool finite3(const double v[3]) {
     return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+// A robot position whose origin index fits int32 with room to spare.
+bool position_ok(const vg_params *p, const double pos[3]) {
+    if (!finite3(pos)) return false;
+    for (int k = 0; k < 3; ++k)
+        if (std::fabs(pos[k] / (double)p->vox_size) >= 1073741824.0) return false;
+    return true;
 }
 
 bool params_ok(const vg_params *p) {
@@ -144,6 +158,17 @@ void bundle_of(const vg_params *p, int32_t &vd, int32_t &hw, int32_t &hh) {
 void origin_of(const vg_params *p, const double pos[3], int32_t o[3]) {
     for (int k = 0; k < 3; ++k)
         o[k] = (int32_t)floor(pos[k] / (double)p->vox_size) - p->grid_size[k] / 2;
+}
+
+// delta = o2 - o1, with an axis whose offset is the grid's size or more
+// (nothing survives the shift) set to the size, so that index sums in the
+// kernels stay small.
+void shift_delta(const vg_params *p, const int32_t o1[3], const int32_t o2[3], int32_t d[3]) {
+    for (int k = 0; k < 3; ++k) {
+        const int64_t v = (int64_t)o2[k] - o1[k];
+        const int64_t n = p->grid_size[k];
+        d[k] = (int32_t)(v >= n ? n : (v <= -n ? -n : v));
+    }
 }
 
 // Composes T^v_c.  Rejects poses that are not finite, whose rotation block
@@ -267,6 +292,16 @@ cudaError_t launch(vg_grid *G, int kind, cudaStream_t s, F &&fn) {
 }
 
 // K2..K4 after K1 has filled occ_raw.
+// Applies a pending re-centre on its own (K5): loc shifted into loc_alt.
+cudaError_t apply_pending(vg_grid *G, cudaStream_t s) {
+    if (!G->pend_on) return cudaSuccess;
+    cudaError_t e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, G->pend, G->loc, G->loc_alt, s); });
+    if (e != cudaSuccess) return e;
+    std::swap(G->loc, G->loc_alt);
+    G->pend_on = false;
+    return cudaSuccess;
+}
+
 cudaError_t finish_frame(vg_grid *G, FrameArgs &a, cudaStream_t s) {
     cudaError_t e;
     if (a.r > 0) {
@@ -278,7 +313,14 @@ cudaError_t finish_frame(vg_grid *G, FrameArgs &a, cudaStream_t s) {
     const int lpr = G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh);
     e = launch(G, VG_K_RAYTRACE, s, [&] { return vg::launch_raytrace(a, lpr, s); });
     if (e != cudaSuccess) return e;
-    return launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge(a, s); });
+    if (!G->pend_on) return launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge(a, s); });
+    // the measurement is in the re-centred frame: merge it over the shifted
+    // grid, written whole into loc_alt
+    e = launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge_shift(a, G->pend, G->loc_alt, s); });
+    if (e != cudaSuccess) return e;
+    std::swap(G->loc, G->loc_alt);
+    G->pend_on = false;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -312,7 +354,7 @@ int64_t vg_ray_bundle(const vg_params *params, int32_t out[3]) {
 int vg_create(const vg_params *params, const double robot_pos_w[3], void *stream, vg_grid **out) {
     if (!out) return VG_EINVAL;
     *out = nullptr;
-    if (!params_ok(params) || !robot_pos_w || !finite3(robot_pos_w)) return VG_EINVAL;
+    if (!params_ok(params) || !robot_pos_w || !position_ok(params, robot_pos_w)) return VG_EINVAL;
     vg_grid *G = new (std::nothrow) vg_grid();
     if (!G) return VG_ENOMEM;
     G->p = *params;
@@ -467,27 +509,19 @@ int vg_integrate_points(vg_grid *G, const float *xyz, int32_t mem, int64_t n, co
 }
 
 int vg_shift(vg_grid *G, const double robot_pos_w[3], void *stream) {
-    if (!G || !robot_pos_w || !finite3(robot_pos_w)) return VG_EINVAL;
-    int32_t o2[3];
+    if (!G || !robot_pos_w || !position_ok(&G->p, robot_pos_w)) return VG_EINVAL;
+    int32_t o2[3], delta[3];
     origin_of(&G->p, robot_pos_w, o2);
-    const int32_t delta[3] = {o2[0] - G->origin[0], o2[1] - G->origin[1], o2[2] - G->origin[2]};
+    shift_delta(&G->p, G->origin, o2, delta);
     if (delta[0] == 0 && delta[1] == 0 && delta[2] == 0) return VG_OK;
     DeviceGuard dg(G->device);
     if (!dg.ok) return VG_ECUDA;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e;
-    if (std::abs((int64_t)delta[0]) >= G->g.nx || std::abs((int64_t)delta[1]) >= G->g.ny ||
-        std::abs((int64_t)delta[2]) >= G->g.nz) {
-        e = cudaMemsetAsync(G->loc, 0, (size_t)G->g.nvox, s);   // nothing survives
-    } else {
-        e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, delta, G->loc, G->loc_alt, s); });
-        if (e == cudaSuccess) {
-            uint8_t *t = G->loc;
-            G->loc = G->loc_alt;
-            G->loc_alt = t;
-        }
-    }
+    // two re-centres do not compose into one (a voxel shifted out and back
+    // is unknown), so an earlier one is applied first
+    cudaError_t e = apply_pending(G, (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
+    std::memcpy(G->pend, delta, sizeof(delta));
+    G->pend_on = true;
     std::memcpy(G->origin, o2, sizeof(o2));
     return VG_OK;
 }
@@ -499,7 +533,8 @@ int vg_read(vg_grid *G, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes, int32_
     DeviceGuard dg(G->device);
     if (!dg.ok) return VG_ECUDA;
     const cudaMemcpyKind kind = dst_mem == VG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    cudaError_t e = cudaMemcpyAsync(dst, G->loc, (size_t)G->g.nvox, kind, (cudaStream_t)stream);
+    cudaError_t e = apply_pending(G, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, G->loc, (size_t)G->g.nvox, kind, (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
     if (origin) std::memcpy(origin, G->origin, sizeof(G->origin));
     return VG_OK;
@@ -514,6 +549,7 @@ int vg_write(vg_grid *G, const uint8_t *src, int32_t src_mem, int64_t src_bytes,
     const cudaMemcpyKind kind = src_mem == VG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaMemcpyAsync(G->loc, src, (size_t)G->g.nvox, kind, (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
+    G->pend_on = false;   // replaced whole
     std::memcpy(G->origin, origin, sizeof(G->origin));
     return VG_OK;
 }
@@ -600,7 +636,7 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
         if (f.dtype != VG_DEPTH_F32 && f.dtype != VG_DEPTH_U16) return VG_EINVAL;
         if (f.dtype == VG_DEPTH_U16 && !(std::isfinite(f.depth_scale) && f.depth_scale > 0.0f)) return VG_EINVAL;
         if (G->device != B->device || G->p.vox_inf > 3) return VG_EINVAL;
-        if (f.recentre && !finite3(f.robot_pos_w)) return VG_EINVAL;
+        if (f.recentre && !position_ok(&G->p, f.robot_pos_w)) return VG_EINVAL;
         vg::Pose32 T;
         if (!pose_of(G, f.T_wc, T)) return VG_EINVAL;
         seen.push_back(G);
@@ -616,7 +652,7 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
     }
     vg::BatchCtl *ctl = reinterpret_cast<vg::BatchCtl *>(B->host);
     vg::BatchItem *items = reinterpret_cast<vg::BatchItem *>(B->host + sizeof(vg::BatchCtl));
-    int64_t total[5] = {0, 0, 0, 0, 0};
+    int64_t total[4] = {0, 0, 0, 0};
     for (int32_t i = 0; i < n; ++i) {
         const vg_frame &f = frames[i];
         vg_grid *G = f.grid;
@@ -642,33 +678,37 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
             ((npix + 3) / 4 + 255) / 256,
             G->p.vox_inf > 0 ? (int64_t)it.tiles[0] * it.tiles[1] * it.tiles[2] : 0,
             (nrays + (256 / it.lpr) - 1) / (256 / it.lpr),
-            (G->g.words + 255) / 256,
-            0};
-        int64_t u5 = 0;
+            (G->g.words + 255) / 256};
+        if (G->pend_on) {
+            // the grid's pending re-centre is applied by this step's merge,
+            // which writes the grid whole into loc_alt
+            it.dx = G->pend[0];
+            it.dy = G->pend[1];
+            it.dz = G->pend[2];
+            it.loc_dst = G->loc_alt;
+            std::swap(G->loc, G->loc_alt);
+            G->pend_on = false;
+        }
         if (f.recentre) {
-            int32_t o2[3];
+            // left pending, for the grid's next merge (or read)
+            int32_t o2[3], d[3];
             origin_of(&G->p, f.robot_pos_w, o2);
-            const int32_t d[3] = {o2[0] - G->origin[0], o2[1] - G->origin[1], o2[2] - G->origin[2]};
+            shift_delta(&G->p, G->origin, o2, d);
             if (d[0] || d[1] || d[2]) {
-                it.dx = d[0];
-                it.dy = d[1];
-                it.dz = d[2];
-                it.loc_dst = G->loc_alt;
-                u5 = ((G->g.nvox + 15) / 16 + 255) / 256;
-                // host state after this step: the grid lives in loc_alt at o2
-                std::swap(G->loc, G->loc_alt);
+                std::memcpy(G->pend, d, sizeof(d));
+                G->pend_on = true;
                 std::memcpy(G->origin, o2, sizeof(o2));
             }
         }
-        for (int p = 0; p < 5; ++p) {
+        for (int p = 0; p < 4; ++p) {
             it.off[p] = total[p];
-            total[p] += (p == 4) ? u5 : units[p];
+            total[p] += units[p];
         }
         ++G->frames;
     }
     std::memset(ctl, 0, sizeof(*ctl));
     ctl->n = n;
-    for (int p = 0; p < 5; ++p) ctl->total[p] = total[p];
+    for (int p = 0; p < 4; ++p) ctl->total[p] = total[p];
     B->bytes = sizeof(vg::BatchCtl) + (size_t)n * sizeof(vg::BatchItem);
     B->prepared = true;
     return VG_OK;

@@ -15,9 +15,37 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace vg {
+
+// Programmatic dependent launch (sm_90 and later).  The one-step kernels
+// are launched with programmatic stream serialization allowed, so a kernel
+// may start while the kernel before it in the stream still runs.  Each lets
+// its successor launch at once (pdl_trigger) and, before it touches any
+// memory that earlier work in the stream writes or reads, waits until its
+// predecessor has completed and that kernel's writes are visible (pdl_wait).
+// Every such kernel waits in every CTA before it ends, so its completion
+// implies its predecessor's, and by induction all earlier work's.  Without
+// a programmatic predecessor both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... P, class... A>
+cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 constexpr int kMaxInflate = 15;
 // In-grid visits a K3 lane keeps in shared memory.  36 entries (36 KB per
@@ -69,7 +97,7 @@ struct FrameArgs {
 // units in each phase.
 struct BatchItem {
     FrameArgs a;
-    int64_t off[5];     // first unit of this frame in phases 1..5
+    int64_t off[4];     // first unit of this frame in phases 1..4
     int32_t tiles[3];   // inflate tile grid (x words / txw, y / 8, z / 8)
     int32_t dtype;      // 0 f32, 1 u16
     int32_t vec;        // depth base aligned for 4-pixel loads
@@ -77,15 +105,15 @@ struct BatchItem {
     int32_t txw;        // inflate tile width in words: 4 or 8
     int32_t align8;     // loc rows and buffer allow 8-byte stores
     int32_t buffered;   // packed visits fit (plane words < 2^26)
-    int32_t dx, dy, dz; // re-centre offset (phase 5)
-    uint8_t *loc_dst;   // re-centred grid (phase 5)
+    int32_t dx, dy, dz; // pending re-centre of the grid, applied by the merge
+    uint8_t *loc_dst;   // non-null: merge a.loc shifted by (dx, dy, dz) into loc_dst
 };
 
 // Control block of a batch launch, copied to the device with the items.
 struct BatchCtl {
     int32_t n;          // frames
     int32_t pad0;
-    int64_t total[5];   // units per phase
+    int64_t total[4];   // units per phase
     unsigned bar_count; // grid barrier: arrivals
     unsigned bar_gen;   // grid barrier: generation
     unsigned error;     // set when a barrier wait ran out
@@ -110,6 +138,8 @@ cudaError_t configure_raytrace(int dev);   // once per device, before the first 
 int auto_lanes_per_ray(int32_t vd, int32_t hw, int32_t hh);
 cudaError_t launch_raytrace(const FrameArgs &a, int lanes_per_ray, cudaStream_t s);
 cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s);
+// K4 over a pending re-centre: reads a.loc shifted by delta, writes every voxel of dst
+cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s);
 cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8_t *src,
                          uint8_t *dst, cudaStream_t s);
 cudaError_t configure_batch(int dev);   // once per device, before the first launch_batch

@@ -320,14 +320,20 @@ __device__ __forceinline__ void frame_start(const FrameArgs &a, float S[3]) {
     for (int k = 0; k < 3; ++k) S[k] = __fdiv_rn(a.T.t[k], a.vs);
 }
 
-// One group of kThreads / LPR rays (group index `group`) of one frame, by
-// all threads of the CTA; `buf` is this CTA's visit buffer (kRtBuf columns of
-// kThreads words).  Returns this thread's in-grid visits.  Warp-synchronous
-// (every lane of every warp must call it; the CTA need not be in step).
-template <int LPR, class L>
-__device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3], const Box &b, int64_t group,
-                                             int buffered, uint32_t *box_fr, uint32_t *box_tr,
-                                             const uint32_t *occ_box, uint32_t *buf) {
+// One lane's share of one ray: the ray's constants, the lane's tau slice
+// and its first voxel.  Depends on the pose and the grid's shape only.
+struct Lane {
+    Ray r;
+    float c_hi;
+    int32_t n0[3];
+    int j;         // lane within the ray
+    bool active;   // the lane has a ray
+};
+
+// Set-up of this thread's lane for group `group` of kThreads / LPR rays.
+// Reads no memory but its arguments.
+template <int LPR>
+__device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], int64_t group, Lane &ln) {
     const int lane = threadIdx.x & 31;
     const int j = lane & (LPR - 1);
     const int32_t width = 2 * a.hw + 1;
@@ -335,16 +341,16 @@ __device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3
     const uint32_t R = 32u * (uint32_t)a.g.wx;   // plane bits per row
     const int rays_per_cta = kThreads / LPR;
     const int64_t ray = group * rays_per_cta + threadIdx.x / LPR;
-    const bool active = ray < nrays;
-    unsigned visits = 0;
-    Ray r;
+    ln.active = ray < nrays;
+    ln.j = j;
+    Ray &r = ln.r;
     r.nx = a.g.nx;
     r.ny = a.g.ny;
     r.nz = a.g.nz;
     float absD[3];
     {
-        const int32_t ra = active ? (int32_t)(ray % width) - a.hw : 0;
-        const int32_t rb = active ? (int32_t)(ray / width) - a.hh : 0;
+        const int32_t ra = ln.active ? (int32_t)(ray % width) - a.hw : 0;
+        const int32_t rb = ln.active ? (int32_t)(ray / width) - a.hh : 0;
         const float fa = (float)ra, fb = (float)rb, fvd = (float)a.vd;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -372,7 +378,7 @@ __device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3
     // this lane's slice of tau: the in-grid part of the segment is cut
     // into LPR equal pieces (any cuts give the same visits as long as
     // neighbouring lanes agree on them and the last lane ends at 1)
-    float c_lo, c_hi;
+    float c_lo;
     {
         float ts = 0.0f, te = 1.0f;
         const float nk[3] = {(float)a.g.nx, (float)a.g.ny, (float)a.g.nz};
@@ -391,13 +397,28 @@ __device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3
         }
         const float span = __fsub_rn(te, ts);
         c_lo = __fadd_rn(ts, __fmul_rn(span, (float)j / (float)LPR));
-        c_hi = (j == LPR - 1) ? 1.0f : __fadd_rn(ts, __fmul_rn(span, (float)(j + 1) / (float)LPR));
+        ln.c_hi = (j == LPR - 1) ? 1.0f : __fadd_rn(ts, __fmul_rn(span, (float)(j + 1) / (float)LPR));
     }
-    int32_t n0[3] = {0, 0, 0};
-    if (j > 0) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) n0[k] = crossings_before(r, k, absD[k], c_lo);
-    }
+    for (int k = 0; k < 3; ++k) ln.n0[k] = j > 0 ? crossings_before(r, k, absD[k], c_lo) : 0;
+}
+
+// The walk of one group of rays set up by rt_setup, by all threads of the
+// CTA; `buf` is this CTA's visit buffer (kRtBuf columns of kThreads words).
+// Returns this thread's in-grid visits.  Warp-synchronous (every lane of
+// every warp must call it; the CTA need not be in step).
+template <int LPR, class L>
+__device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, const Box &b, int buffered,
+                                            uint32_t *box_fr, uint32_t *box_tr, const uint32_t *occ_box,
+                                            uint32_t *buf) {
+    const int lane = threadIdx.x & 31;
+    const int j = ln.j;
+    const bool active = ln.active;
+    const Ray &r = ln.r;
+    const float c_hi = ln.c_hi;
+    const int32_t *n0 = ln.n0;
+    const uint32_t R = 32u * (uint32_t)a.g.wx;
+    unsigned visits = 0;
 
     // ---- pass 1: walk the slice once, keep its in-grid visits --------
     int32_t nvis = 0, hit_at = -1;
@@ -455,6 +476,16 @@ __device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3
         visits += walk_marks(a, r, n0, j == 0, c_hi, b, mode, hit_at, box_fr, box_tr, R);
     }
     return visits;
+}
+
+// One group of rays: rt_setup then rt_walk.
+template <int LPR, class L>
+__device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3], const Box &b, int64_t group,
+                                             int buffered, uint32_t *box_fr, uint32_t *box_tr,
+                                             const uint32_t *occ_box, uint32_t *buf) {
+    Lane ln;
+    rt_setup<LPR>(a, S, group, ln);
+    return rt_walk<LPR, L>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
 }
 
 }  // namespace rt

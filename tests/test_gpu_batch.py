@@ -94,6 +94,32 @@ def test_batch_without_recentre_and_single_frame(vg):
     gb.close()
 
 
+def test_batch_applies_a_pending_shift(vg):
+    # a re-centre made with vg_shift before the step, and the step's own
+    # re-centre left pending after it, read back both ways
+    w = make("robot", robot=7, frames=3)
+    gp, gb = _grid(vg, w), _grid(vg, w)
+    batch = vg.Batch(2)
+    f0, f1, f2 = w.frames
+    for g in (gp, gb):
+        g.shift(f0.robot_pos + np.array([0.3, -0.2, 0.1]))
+    d1, d2 = torch.from_numpy(f1.depth).cuda(), torch.from_numpy(f2.depth).cuda()
+    gp.integrate_depth(d1, f1.T_wc, w.cam.scale)
+    gp.shift(f1.robot_pos)
+    batch.step([(gb, d1, f1.T_wc, f1.robot_pos, w.cam.scale)])
+    assert batch.status() == vg.VG_OK
+    _compare([gp], [gb], "after the step")              # the read applies the pending re-centre
+    gp.shift(f2.robot_pos)
+    gb.shift(f2.robot_pos)
+    gp.integrate_depth(d2, f2.T_wc, w.cam.scale)
+    batch.step([(gb, d2, f2.T_wc, None, w.cam.scale)])
+    assert batch.status() == vg.VG_OK
+    _compare([gp], [gb], "after a step over a vg_shift")
+    batch.close()
+    gp.close()
+    gb.close()
+
+
 def test_batch_replayed_from_a_cuda_graph(vg):
     ws = [make("robot", robot=i, frames=4) for i in range(10, 14)]
     plain = [_grid(vg, w) for w in ws]

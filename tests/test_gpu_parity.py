@@ -85,6 +85,10 @@ class Pair:
 
 
 def run_workload(vg, w, nframes, lanes=None, device=True, shift=True):
+    """Frames with a re-centre after each.  A grid is read (and compared)
+    after every frame but not after its re-centre, so the re-centre is
+    still pending when the next frame comes and that frame's merge applies
+    it; the last re-centre is applied on its own by the final read."""
     g = w.grid
     f0 = w.frames[0]
     P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, f0.robot_pos, lanes)
@@ -95,7 +99,8 @@ def run_workload(vg, w, nframes, lanes=None, device=True, shift=True):
             P.check("%s frame %d" % (w.name, i))
             if shift:
                 P.shift(f.robot_pos, check=False)
-                P.check("%s shift after frame %d" % (w.name, i))
+        if shift:
+            P.check("%s shift after frame %d" % (w.name, nframes - 1))
         got, _ = P.read()
         return got
     finally:
@@ -215,14 +220,14 @@ def test_inflation_radii(vg, r):
 
 
 @pytest.mark.parametrize("n", [(1, 1, 1), (1, 17, 1), (33, 1, 2), (45, 31, 7), (31, 9, 5), (64, 64, 8),
-                               (129, 3, 4)])
+                               (129, 3, 4), (8500, 3, 2)])
 def test_grid_shapes(vg, n):
     rng = np.random.default_rng(sum(n))
     P = _pair(vg, n=n, vs=0.1, r=1, pos=(0.0, 0.0, 0.0))
     for k in range(3):
         d = rng.uniform(0.05, 3.0, size=(24, 32)).astype(np.float32)
         P.depth(d, body_pose([0.0, 0.0, 0.0], rng.uniform(-3, 3), rng.uniform(-0.5, 0.5)))
-        P.shift(rng.uniform(-0.3, 0.3, 3))
+        P.shift(rng.uniform(-0.3, 0.3, 3), check=(k == 2))   # else merged by the next frame
     P.close()
 
 
@@ -256,16 +261,53 @@ def test_axis_aligned_rays(vg):
     P.close()
 
 
-def test_shifts(vg):
+@pytest.mark.parametrize("read_after_shift", [True, False])
+def test_shifts(vg, read_after_shift):
+    # read_after_shift: each re-centre is applied on its own (K5) by the
+    # read; else the next frame's merge applies it
     rng = np.random.default_rng(13)
     P = _pair(vg, n=(30, 20, 10), pos=(0.0, 0.0, 0.0))
     P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([0, 0, 0]))
     pos = np.zeros(3)
     for step in ([0.1, 0, 0], [0, -0.25, 0.1], [-0.33, 0.47, -0.2], [0, 0, 0], [2.9, 0, 0], [0, 0, 5.0],
-                 [-0.05, 0.05, 0.0]):
+                 [-0.05, 0.05, 0.0], [-3.1, 0.0, 0.0], [0.0, 2.1, -1.1]):
         pos = pos + np.array(step)
-        P.shift(pos)
+        P.shift(pos, check=read_after_shift)
         P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose(pos, rng.uniform(-3, 3)))
+    P.close()
+
+
+def test_shifts_in_a_row_do_not_compose(vg):
+    # out by 5 voxels and back: the voxels that left are unknown, so the
+    # second re-centre cannot be folded into the first
+    rng = np.random.default_rng(14)
+    P = _pair(vg, n=(30, 20, 10), pos=(0.0, 0.0, 0.0))
+    P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([0, 0, 0]))
+    P.shift([0.5, 0.0, 0.0], check=False)
+    P.shift([0.0, 0.0, 0.0], check=False)
+    P.check("out and back")
+    P.shift([0.0, -0.7, 0.3], check=False)
+    P.shift([0.4, -0.7, 0.3], check=False)
+    P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([0.4, -0.7, 0.3], 1.0))
+    P.shift([40.0, 0.0, 0.0], check=False)             # nothing survives
+    P.shift([40.3, 0.0, 0.0], check=False)
+    P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([40.3, 0.0, 0.0], -1.0))
+    P.shift([40.3, 0.0, 0.2], check=False)
+    P.check("last")
+    P.close()
+
+
+def test_write_replaces_a_pending_shift(vg):
+    rng = np.random.default_rng(15)
+    P = _pair(vg, n=(40, 30, 16))
+    P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([0.1, 0.2, 0.3], 0.2))
+    P.shift([0.6, -0.4, 0.2], check=False)
+    prior = rng.integers(0, 4, size=P.g.shape).astype(np.uint8)
+    origin = np.array([3, -2, 1], np.int32)
+    P.g.write(prior.ravel().copy(), origin)
+    P.o.loc = prior.copy()
+    P.o.o = origin.copy()
+    P.check("write over a pending shift")
     P.close()
 
 
@@ -350,4 +392,6 @@ def test_bad_arguments_on_device(vg):
     small = torch.empty(10, dtype=torch.uint8, device="cuda")
     with pytest.raises(vg.VGError):
         P.g.read(small)
+    with pytest.raises(vg.VGError):
+        P.g.shift((1e12, 0.0, 0.0))     # origin index beyond int32
     P.close()

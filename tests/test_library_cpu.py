@@ -98,10 +98,12 @@ def test_create_rejects_bad_params(vg, field, value):
     assert e.value.status == vg.VG_EINVAL
 
 
-def test_create_rejects_non_finite_position(vg):
+@pytest.mark.parametrize("pos", [(0.0, float("inf"), 0.0), (0.0, 0.0, float("nan")), (2.0e8, 0.0, 0.0)])
+def test_create_rejects_unusable_position(vg, pos):
+    # not finite, or an origin index (pos / vox_size) of 2^30 or more
     p = vg.make_params((10, 10, 10), 0.1, 87, 58, 4.0, 1)
     with pytest.raises(vg.VGError) as e:
-        vg.vg_create(p, (0.0, float("inf"), 0.0), stream=0)
+        vg.vg_create(p, pos, stream=0)
     assert e.value.status == vg.VG_EINVAL
 
 
