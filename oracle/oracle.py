@@ -14,6 +14,7 @@ from . import build as _build
 
 UNK, FREE, OCC, TRACED = 0, 1, 2, 3
 DEPTH_F32, DEPTH_U16 = 0, 1
+LIT_INFLATE_AFTER_TRACE, LIT_SKIP_START, LIT_LOC_OCCUPANCY = 1, 2, 4
 
 
 @dataclasses.dataclass(frozen=True)
@@ -25,6 +26,7 @@ class OracleParams:
     fov_y_deg: float
     depth: float
     vox_inf: int
+    literal: int = 0   # LIT_* flags; 0 is the default reading
 
     @property
     def shape(self):
@@ -37,7 +39,8 @@ class OracleParams:
 
 class _CParams(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("vox_size", C.c_float), ("fov_x_deg", C.c_float),
-                ("fov_y_deg", C.c_float), ("depth", C.c_float), ("vox_inf", C.c_int32)]
+                ("fov_y_deg", C.c_float), ("depth", C.c_float), ("vox_inf", C.c_int32),
+                ("literal", C.c_uint32)]
 
 
 class _CPose(C.Structure):
@@ -53,6 +56,7 @@ def _cparams(p):
     c.fov_y_deg = p.fov_y_deg
     c.depth = p.depth
     c.vox_inf = int(p.vox_inf)
+    c.literal = int(p.literal)
     return c
 
 
@@ -100,9 +104,9 @@ class Oracle:
             "or_voxelize_points": (i64, [vp, vp, vp, i64, vp]),
             "or_inflate": (None, [vp, vp, vp]),
             "or_add_occ_literal_depth": (i64, [vp, vp, vp, i32, i32, i32, f32, vp]),
-            "or_dda": (i64, [vp, vp, vp, vp, i64]),
+            "or_dda": (i64, [vp, vp, vp, C.c_uint32, vp, i64]),
             "or_raytrace": (i64, [vp, vp, vp, vp, vp, vp]),
-            "or_resolve": (None, [i64, vp, vp, vp, vp]),
+            "or_resolve": (None, [i64, C.c_uint32, vp, vp, vp, vp]),
             "or_merge": (None, [i64, vp, vp]),
             "or_shift": (None, [vp, vp, vp, vp]),
             "or_integrate_depth": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, f32, vp, vp]),
@@ -180,13 +184,13 @@ class Oracle:
         return occ_inf
 
     # --- Alg. 2 -------------------------------------------------------------
-    def dda(self, n, S, D, cap=1 << 16):
+    def dda(self, n, S, D, cap=1 << 16, literal=0):
         out = np.zeros((cap, 3), np.int32)
         S = np.ascontiguousarray(np.asarray(S, np.float32))
         D = np.ascontiguousarray(np.asarray(D, np.float32))
-        cnt = self._L.or_dda(_ptr(_i32(n)), _ptr(S), _ptr(D), _ptr(out), cap)
+        cnt = self._L.or_dda(_ptr(_i32(n)), _ptr(S), _ptr(D), int(literal), _ptr(out), cap)
         if cnt > cap:
-            return self.dda(n, S, D, cap=int(cnt))
+            return self.dda(n, S, D, cap=int(cnt), literal=literal)
         return out[:cnt].copy()
 
     def raytrace(self, p, pose, occ_inf, ray_order=None):
@@ -203,10 +207,10 @@ class Oracle:
         return fr, tr, int(visits)
 
     # --- resolve / Alg. 3 / shift ---------------------------------------------
-    def resolve(self, occ_inf, fr, tr):
+    def resolve(self, occ_inf, fr, tr, literal=0):
         occ_inf, fr, tr = (np.ascontiguousarray(a, np.uint8) for a in (occ_inf, fr, tr))
         ms = np.zeros_like(occ_inf)
-        self._L.or_resolve(occ_inf.size, _ptr(occ_inf), _ptr(fr), _ptr(tr), _ptr(ms))
+        self._L.or_resolve(occ_inf.size, int(literal), _ptr(occ_inf), _ptr(fr), _ptr(tr), _ptr(ms))
         return ms
 
     def merge(self, ms, loc):

@@ -210,7 +210,7 @@ int64_t or_add_occ_literal_depth(const or_params *p, const or_pose *T, const voi
  */
 typedef void (*visit_fn)(void *ctx, int32_t x, int32_t y, int32_t z);
 
-static int64_t dda_walk(const int32_t n[3], const float S[3], const float D[3],
+static int64_t dda_walk(const int32_t n[3], const float S[3], const float D[3], int skip_start,
                         visit_fn visit, void *ctx) {
     int32_t i[3], step[3];
     float inv[3], tmax[3];
@@ -230,8 +230,11 @@ static int64_t dda_walk(const int32_t n[3], const float S[3], const float D[3],
         }
     }
     int64_t visits = 0;
+    int first = 1;
     for (;;) {
-        if (in_grid(n, i[0], i[1], i[2])) {
+        if (first && skip_start) {
+            /* the literal reading moves before its first test */
+        } else if (in_grid(n, i[0], i[1], i[2])) {
             visit(ctx, i[0], i[1], i[2]);
             ++visits;
         } else {
@@ -242,6 +245,7 @@ static int64_t dda_walk(const int32_t n[3], const float S[3], const float D[3],
             }
             if (gone) break;
         }
+        first = 0;
         int m = 0;
         if (tmax[1] < tmax[m]) m = 1;
         if (tmax[2] < tmax[m]) m = 2;
@@ -269,10 +273,10 @@ static void list_visit(void *c, int32_t x, int32_t y, int32_t z) {
     ++L->count;
 }
 
-int64_t or_dda(const int32_t n[3], const float S[3], const float D[3], int32_t *out,
-               int64_t cap) {
+int64_t or_dda(const int32_t n[3], const float S[3], const float D[3], uint32_t literal,
+               int32_t *out, int64_t cap) {
     list_ctx L = {out, cap, 0};
-    dda_walk(n, S, D, list_visit, &L);
+    dda_walk(n, S, D, (literal & OR_LIT_SKIP_START) != 0, list_visit, &L);
     return L.count;
 }
 
@@ -325,20 +329,24 @@ int64_t or_raytrace(const or_params *p, const or_pose *T, const uint8_t *occ_inf
             D[k] = d;
         }
         ray_ctx R = {p->n, occ_inf, fr, tr, 0};
-        visits += dda_walk(p->n, S, D, ray_visit, &R);
+        visits += dda_walk(p->n, S, D, (p->literal & OR_LIT_SKIP_START) != 0, ray_visit, &R);
     }
     return visits;
 }
 
-void or_resolve(int64_t nvox, const uint8_t *occ_inf, const uint8_t *fr,
+void or_resolve(int64_t nvox, uint32_t literal, const uint8_t *occ_inf, const uint8_t *fr,
                 const uint8_t *tr, uint8_t *ms) {
     /* Precedence occupied > free > traced > unknown: a voxel any ray saw
      * free before its obstacle is free (reading of the concurrent-write
-     * remark of Sec. IV-C). */
+     * remark of Sec. IV-C).  In the loc_grid reading the rays do not see
+     * this measurement's occupied voxels and Alg. 2's writes replace them:
+     * free > traced > occupied > unknown. */
+    const int rays_last = (literal & OR_LIT_LOC_OCCUPANCY) != 0;
     for (int64_t i = 0; i < nvox; ++i) {
-        if (occ_inf[i]) ms[i] = OR_OCC;
+        if (occ_inf[i] && !rays_last) ms[i] = OR_OCC;
         else if (fr[i]) ms[i] = OR_FREE;
         else if (tr[i]) ms[i] = OR_TRACED;
+        else if (occ_inf[i]) ms[i] = OR_OCC;
         else ms[i] = OR_UNK;
     }
 }
@@ -370,8 +378,17 @@ static int finish_frame(const or_params *p, const or_pose *T, uint8_t *occ_raw,
     int rc = -1;
     if (occ_inf && fr && tr && ms) {
         or_inflate(p, occ_raw, occ_inf);
-        or_raytrace(p, T, occ_inf, NULL, fr, tr);
-        or_resolve(nv, occ_inf, fr, tr, ms);
+        /* the grid the rays test: Alg. 1's order (inflated), the kernel
+         * list's order (raw), or Alg. 2's literal loc_grid (the grid before
+         * this measurement; the ms scratch holds it until the resolve) */
+        const uint8_t *tested = occ_inf;
+        if (p->literal & OR_LIT_INFLATE_AFTER_TRACE) tested = occ_raw;
+        if (p->literal & OR_LIT_LOC_OCCUPANCY) {
+            for (int64_t i = 0; i < nv; ++i) ms[i] = loc[i] == OR_OCC;
+            tested = ms;
+        }
+        or_raytrace(p, T, tested, NULL, fr, tr);
+        or_resolve(nv, p->literal, occ_inf, fr, tr, ms);
         or_merge(nv, ms, loc);
         if (ms_out) memcpy(ms_out, ms, (size_t)nv);
         rc = 0;

@@ -36,6 +36,22 @@ extern "C" {
 enum { OR_UNK = 0, OR_FREE = 1, OR_OCC = 2, OR_TRACED = 3 };
 enum { OR_DEPTH_F32 = 0, OR_DEPTH_U16 = 1 };
 
+/* Literal readings of passages the default reading interprets (bit flags,
+ * for comparison with the default; 0 is the default reading):
+ *  OR_LIT_INFLATE_AFTER_TRACE  rays test the occupancy before inflation;
+ *                              the inflation still marks its voxels
+ *                              occupied (the order in which the kernel
+ *                              list names the steps, trace before inflate).
+ *  OR_LIT_SKIP_START           Alg. 2 moves by a voxel before its first
+ *                              test, so a ray's start voxel is not visited.
+ *  OR_LIT_LOC_OCCUPANCY        Alg. 2 tests loc_grid (the grid before this
+ *                              measurement) for occupied voxels, and its
+ *                              writes of the ray state replace the
+ *                              measurement grid's occupied mark.
+ * INFLATE_AFTER_TRACE and LOC_OCCUPANCY both choose the tested grid; when
+ * both are set LOC_OCCUPANCY decides. */
+enum { OR_LIT_INFLATE_AFTER_TRACE = 1, OR_LIT_SKIP_START = 2, OR_LIT_LOC_OCCUPANCY = 4 };
+
 /* Table I parameters.  n = grid_size in voxels (x, y, z). */
 typedef struct {
     int32_t n[3];
@@ -44,6 +60,7 @@ typedef struct {
     float fov_y_deg;
     float depth;
     int32_t vox_inf;
+    uint32_t literal;   /* OR_LIT_* flags, 0 for the default reading */
 } or_params;
 
 /* T^v_c rounded to float: R row-major (3x3), t in metres. */
@@ -104,21 +121,26 @@ int64_t or_add_occ_literal_depth(const or_params *p, const or_pose *T, const voi
 /* Amanatides-Woo traversal (Alg. 2) of the segment S + tau*D, tau in [0,1],
  * in voxel units.  Writes the in-grid voxels visited, in visit order, as
  * (x, y, z) triples into out (up to cap triples) and returns how many were
- * visited (which may exceed cap; then only cap are written). */
-int64_t or_dda(const int32_t n[3], const float S[3], const float D[3],
+ * visited (which may exceed cap; then only cap are written).  literal:
+ * OR_LIT_SKIP_START leaves out the start voxel; other bits are ignored. */
+int64_t or_dda(const int32_t n[3], const float S[3], const float D[3], uint32_t literal,
                int32_t *out, int64_t cap);
 
 /* Alg. 2 over the whole bundle.  For each ray, voxels before the first
- * occupied (occ_inf) voxel get fr = 1, voxels after it get tr = 1, occupied
- * voxels are never written.  ray_order, if not NULL, is a permutation of
+ * occupied voxel of occ_inf (the grid the rays test: the inflated
+ * occupancy, or what p->literal chooses) get fr = 1, voxels after it get
+ * tr = 1, occupied voxels are never written.  p->literal's
+ * OR_LIT_SKIP_START applies to every ray.  ray_order, if not NULL, is a permutation of
  * the ray ids (id = (b+hh)*(2hw+1) + (a+hw)) giving the processing order.
  * Returns the number of in-grid voxel visits. */
 int64_t or_raytrace(const or_params *p, const or_pose *T, const uint8_t *occ_inf,
                     const int64_t *ray_order, uint8_t *fr, uint8_t *tr);
 
 /* Measurement-grid state of every voxel: OCC if occ_inf, else FREE if fr,
- * else TRACED if tr, else UNK. */
-void or_resolve(int64_t nvox, const uint8_t *occ_inf, const uint8_t *fr,
+ * else TRACED if tr, else UNK.  With OR_LIT_LOC_OCCUPANCY in literal the
+ * rays' writes come after the occupied marks: FREE if fr, else TRACED if
+ * tr, else OCC if occ_inf, else UNK. */
+void or_resolve(int64_t nvox, uint32_t literal, const uint8_t *occ_inf, const uint8_t *fr,
                 const uint8_t *tr, uint8_t *ms);
 
 /* Alg. 3: loc[idx] = ms[idx] wherever ms[idx] != UNK. */
@@ -130,7 +152,8 @@ void or_shift(const int32_t n[3], const int32_t delta[3], const uint8_t *src,
               uint8_t *dst);
 
 /* One whole measurement (steps 2-4 of Sec. IV) on a depth image: voxelize,
- * inflate, ray-trace, resolve, merge into loc (in place).  o is the current
+ * inflate, ray-trace, resolve, merge into loc (in place), in the reading
+ * p->literal selects.  o is the current
  * grid origin.  ms_out, if not NULL, receives the resolved measurement grid.
  * Returns 0, or -1 if scratch memory could not be allocated. */
 int or_integrate_depth(const or_params *p, const int32_t o[3], const double T_wc[16],

@@ -21,6 +21,7 @@ import scipy.ndimage as ndi
 
 from oracle import OracleParams
 from oracle.oracle import FREE, OCC, TRACED, UNK
+from oracle.oracle import LIT_INFLATE_AFTER_TRACE, LIT_LOC_OCCUPANCY, LIT_SKIP_START
 
 import bruteforce as bf
 
@@ -32,9 +33,9 @@ EPS_EXACT_SEGMENT = 1e-5
 EPS_GEOMETRIC = 2e-4
 
 
-def _p(n, vs, fx=87.0, fy=58.0, depth=4.0, r=1):
+def _p(n, vs, fx=87.0, fy=58.0, depth=4.0, r=1, literal=0):
     return OracleParams(tuple(int(v) for v in n), float(vs), float(fx), float(fy),
-                        float(depth), int(r))
+                        float(depth), int(r), int(literal))
 
 
 # --------------------------------------------------------------------------
@@ -433,6 +434,132 @@ def check_rays_stop_at_inflated_voxels(orc):
     assert seen_free > 0 and seen_traced > 0, (seen_free, seen_traced)
 
 
+# --------------------------------------------------------------------------
+# The literal readings (comparison flags): each pinned by brute force or a
+# closed form of its own, and against the default where they must agree
+# --------------------------------------------------------------------------
+def check_skip_start_walks(orc):
+    # "move by a voxel" before the first test: the walk is the segment's
+    # crossed voxels without the start voxel floor(S)
+    rng = np.random.default_rng(52)
+    n = (12, 10, 9)
+    for _ in range(300):
+        S = rng.uniform(-2, 14, 3).astype(np.float32)
+        D = rng.uniform(-14, 14, 3).astype(np.float32)
+        if rng.random() < 0.2:
+            D[rng.integers(3)] = 0.0
+        start = tuple(int(v) for v in np.floor(S))
+        vis = orc.dda(n, S, D, literal=LIT_SKIP_START)
+        got = [tuple(v) for v in vis.tolist()]
+        assert start not in got, (S, D)
+        inside = all(0 <= start[k] < n[k] for k in range(3))
+        _walk_ok(np.array(([start] if inside else []) + got, np.int32).reshape(-1, 3), n, S, D,
+                 EPS_EXACT_SEGMENT)
+    # hand walk: the first case of the default's hand list without its start
+    got = [tuple(v) for v in orc.dda((8, 8, 8), np.float32((0.5, 0.5, 0.5)), np.float32((2, 2, 0)),
+                                     literal=LIT_SKIP_START).tolist()]
+    assert got == [(1, 0, 0), (1, 1, 0), (2, 1, 0), (2, 2, 0)], got
+
+
+def check_skip_start_leaves_camera_voxel(orc):
+    # every ray starts in the camera's voxel and walks away from it, so with
+    # the start skipped no ray visits it: an empty frame leaves it unknown
+    # and marks every other crossed voxel free
+    p, T, o, pose = _small_setup(orc, yaw=0.4)
+    ps = _p(p.n, p.vox_size, p.fov_x_deg, p.fov_y_deg, p.depth, p.vox_inf, LIT_SKIP_START)
+    loc = np.zeros(p.shape, np.uint8)
+    ms = orc.integrate_depth(ps, o, T, np.zeros((24, 32), np.float32), 1.0, loc, want_ms=True)
+    cam = np.floor(np.asarray(pose.t, np.float64) / p.vox_size).astype(int)
+    must, may = _bundle_sets(orc, p, T, o)
+    must[cam[2], cam[1], cam[0]] = False
+    assert ms[cam[2], cam[1], cam[0]] == UNK
+    assert np.all(ms[must] == FREE) and np.all(ms[~may] == UNK)
+    assert not np.any(ms == OCC) and not np.any(ms == TRACED)
+
+
+def _point_shadow(orc, p, pos, w, blocker_lo, blocker_hi, ms):
+    # behind a single obstacle point w: a voxel some ray crosses without
+    # touching the blocker box is free, a voxel only blocker-crossing rays
+    # reach is unknown-and-traced (the blocker is what the rays test)
+    o = orc.origin(p, pos)
+    T = bf.pose_T_wc(pos)
+    (vd, hw, hh), _ = orc.ray_bundle(p)
+    S, D = bf.bundle_segments(p.vox_size, o, T, vd, hw, hh)
+    hit_may = bf.box_overlap(S, D, blocker_lo, blocker_hi) > -EPS_GEOMETRIC
+    hit_must = bf.box_overlap(S, D, blocker_lo, blocker_hi) > EPS_GEOMETRIC
+    c = np.floor(w / p.vox_size).astype(int) - o
+    seen_free = seen_traced = 0
+    for x in range(c[0] + 3, p.n[0]):
+        for y in range(c[1] - 6, c[1] + 7):
+            for z in range(c[2] - 6, c[2] + 7):
+                v = np.array([x, y, z])
+                ov = bf.box_overlap(S, D, v, v + 1)
+                must, may = ov > EPS_GEOMETRIC, ov > -EPS_GEOMETRIC
+                if np.any(must & ~hit_may):
+                    assert ms[z, y, x] == FREE, (v, ms[z, y, x])
+                    seen_free += 1
+                elif np.any(must) and np.all(hit_must[may]):
+                    assert ms[z, y, x] == TRACED, (v, ms[z, y, x])
+                    seen_traced += 1
+    return seen_free, seen_traced
+
+
+def check_inflate_after_trace_rays_see_points(orc):
+    # tracing before inflating: rays stop only at the point's own voxel, yet
+    # the inflated halo is still marked occupied.  Same scene as
+    # check_rays_stop_at_inflated_voxels, where the halo blocks.
+    pos = np.array([0.013, 0.027, 0.031])
+    w = np.array([1.05, 0.05, 0.05])
+    p = _p((40, 32, 16), 0.1, 87.0, 58.0, 3.0, 2, LIT_INFLATE_AFTER_TRACE)
+    o = orc.origin(p, pos)
+    T = bf.pose_T_wc(pos)
+    cam = np.array([-(w[1] - pos[1]), -(w[2] - pos[2]), w[0] - pos[0]], np.float32)
+    loc = np.zeros(p.shape, np.uint8)
+    ms = orc.integrate_points(p, o, T, cam[None, :], loc, want_ms=True)
+    c = np.floor(w / p.vox_size).astype(int) - o
+    assert np.all(ms[c[2] - 2:c[2] + 3, c[1] - 2:c[1] + 3, c[0] - 2:c[0] + 3] == OCC)
+    f, t = _point_shadow(orc, p, pos, w, c, c + 1, ms)
+    assert f > 0 and t > 0, (f, t)
+    # some voxel the halo shadows in the default reading is free here
+    pd = _p((40, 32, 16), 0.1, 87.0, 58.0, 3.0, 2)
+    msd = orc.integrate_points(pd, o, T, cam[None, :], np.zeros(p.shape, np.uint8), want_ms=True)
+    assert np.any((msd == TRACED) & (ms == FREE))
+    assert not np.any((msd == FREE) & (ms == TRACED))
+
+
+def check_loc_reading(orc):
+    # Alg. 2 testing loc_grid: rays stop at an obstacle the grid held before
+    # this measurement (kept occupied, as no ray writes it), and pass through
+    # the measurement's own obstacle, whose voxel they overwrite with free.
+    pos = np.array([0.013, 0.027, 0.031])
+    T = bf.pose_T_wc(pos)
+    p = _p((40, 32, 16), 0.1, 87.0, 58.0, 3.0, 0, LIT_LOC_OCCUPANCY)
+    o = orc.origin(p, pos)
+    old = np.array([1.05, 0.05, 0.05])                    # obstacle in loc only
+    c = np.floor(old / p.vox_size).astype(int) - o
+    prior = np.zeros(p.shape, np.uint8)
+    prior[c[2], c[1], c[0]] = OCC
+    new = np.array([0.55, -0.35, 0.05])                   # obstacle in the frame only, off the old one's line
+    cn = np.floor(new / p.vox_size).astype(int) - o
+    cam = np.array([-(new[1] - pos[1]), -(new[2] - pos[2]), new[0] - pos[0]], np.float32)
+    loc = prior.copy()
+    ms = orc.integrate_points(p, o, T, cam[None, :], loc, want_ms=True)
+    assert ms[cn[2], cn[1], cn[0]] == FREE and loc[cn[2], cn[1], cn[0]] == FREE
+    assert ms[c[2], c[1], c[0]] == UNK and loc[c[2], c[1], c[0]] == OCC
+    f, t = _point_shadow(orc, p, pos, old, c, c + 1, ms)
+    assert f > 0 and t > 0, (f, t)
+    # the default reading: the frame's obstacle is occupied and blocks, the
+    # stale one is crossed and freed
+    pd = _p((40, 32, 16), 0.1, 87.0, 58.0, 3.0, 0)
+    locd = prior.copy()
+    msd = orc.integrate_points(pd, o, T, cam[None, :], locd, want_ms=True)
+    assert msd[cn[2], cn[1], cn[0]] == OCC and locd[c[2], c[1], c[0]] == FREE
+    # the resolve table of this reading: free > traced > occupied > unknown
+    combos = np.array([[a, b, d] for a in (0, 1) for b in (0, 1) for d in (0, 1)], np.uint8)
+    got = orc.resolve(combos[:, 0], combos[:, 1], combos[:, 2], literal=LIT_LOC_OCCUPANCY)
+    assert got.tolist() == [FREE if b else TRACED if d else OCC if a else UNK for a, b, d in combos]
+
+
 def check_resolve_and_merge_tables(orc):
     # resolve: precedence occupied > free > traced > unknown
     combos = np.array([[a, b, c] for a in (0, 1) for b in (0, 1) for c in (0, 1)], np.uint8)
@@ -538,5 +665,7 @@ ALL_CHECKS = [
     check_inflation, check_literal_alg1_equals_dilation, check_dda_bruteforce,
     check_dda_hand_walks, check_empty_frame_all_free, check_wall_closed_form,
     check_occluder_shadow, check_rays_stop_at_inflated_voxels, check_resolve_and_merge_tables, check_untouched_voxels_keep_prior,
+    check_skip_start_walks, check_skip_start_leaves_camera_voxel, check_inflate_after_trace_rays_see_points,
+    check_loc_reading,
     check_order_independence, check_shift, check_grid_follows_robot,
 ]

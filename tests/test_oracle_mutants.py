@@ -34,8 +34,7 @@ MUTANTS = {
                               "return (int64_t)x + (int64_t)n[1] * ((int64_t)y + (int64_t)n[0] * z);"),
     "shift_sign": ("int32_t sx = x + delta[0], sy = y + delta[1], sz = z + delta[2];",
                    "int32_t sx = x - delta[0], sy = y - delta[1], sz = z - delta[2];"),
-    "rays_see_raw_occupancy": ("or_raytrace(p, T, occ_inf, NULL, fr, tr);",
-                               "or_raytrace(p, T, occ_raw, NULL, fr, tr);"),
+    "rays_see_raw_occupancy": ("const uint8_t *tested = occ_inf;", "const uint8_t *tested = occ_raw;"),
     "principal_point_w_over_2": ("K[2] = (float)(((double)W - 1.0) / 2.0);",
                                  "K[2] = (float)((double)W / 2.0);"),
     "never_traced": ("R->traced = 1;", "R->traced = 0;"),
@@ -50,6 +49,15 @@ MUTANTS = {
                             "if (in_grid(n, i[0], i[1], i[2]) && (i[0] != (int32_t)floorf(S[0]) || "
                             "i[1] != (int32_t)floorf(S[1]) || i[2] != (int32_t)floorf(S[2]))) {"),
     "fy_uses_fx": ("xyz[1] = ((float)v - K[3]) * d / K[1];", "xyz[1] = ((float)v - K[3]) * d / K[0];"),
+    # the literal readings
+    "skip_start_ignored_by_rays": ("dda_walk(p->n, S, D, (p->literal & OR_LIT_SKIP_START) != 0, ray_visit, &R)",
+                                   "dda_walk(p->n, S, D, 0, ray_visit, &R)"),
+    "skip_start_skips_two": ("        first = 0;\n", "        first = (first == 1) ? 2 : 0;\n"),
+    "after_trace_tests_inflated": ("if (p->literal & OR_LIT_INFLATE_AFTER_TRACE) tested = occ_raw;",
+                                   "if (p->literal & OR_LIT_INFLATE_AFTER_TRACE) tested = occ_inf;"),
+    "loc_reading_tests_measurement": ("            tested = ms;\n", "            tested = occ_inf;\n"),
+    "loc_reading_keeps_occupied": ("const int rays_last = (literal & OR_LIT_LOC_OCCUPANCY) != 0;",
+                                   "const int rays_last = 0;"),
 }
 
 RUNNER = r"""
