@@ -72,9 +72,30 @@ enum { VG_DEPTH_F32 = 0, VG_DEPTH_U16 = 1 };
 /* Where a buffer lives. */
 enum { VG_MEM_DEVICE = 0, VG_MEM_HOST = 1 };
 
-/* Grid flags. */
+/* Grid flags.  The VG_FLAG_LIT_* bits select literal readings of passages
+ * the default reading interprets, for comparison with it; each changes
+ * results, none is the paper's intent as this library reads it:
+ *  VG_FLAG_LIT_INFLATE_AFTER_TRACE
+ *      rays test the occupancy before inflation (trace, then inflate: the
+ *      order in which the kernel list names the steps); inflated voxels
+ *      are still marked occupied.  Default: Alg. 1 inflates first and rays
+ *      stop at inflated voxels.
+ *  VG_FLAG_LIT_SKIP_START_VOXEL
+ *      Alg. 2 moves by a voxel before its first test, so no ray visits the
+ *      camera's voxel.  Default: the start voxel is visited.
+ *  VG_FLAG_LIT_LOC_OCCUPANCY
+ *      Alg. 2 tests loc_grid (the grid before this measurement, after any
+ *      pending re-centre) for occupied voxels, and the rays' free/traced
+ *      marks replace this measurement's occupied marks: precedence free >
+ *      traced > occupied > unknown.  Default: rays test the measurement's
+ *      inflated occupancy and occupied wins.  Costs one more bit plane.
+ * INFLATE_AFTER_TRACE and LOC_OCCUPANCY exclude each other.  Grids with a
+ * LIT flag take the plain path only (not batches, not the server). */
 enum {
-    VG_FLAG_STATS = 1u << 0   /* count in-grid points and ray-voxel visits (vg_stats) */
+    VG_FLAG_STATS = 1u << 0,                    /* count in-grid points and ray-voxel visits (vg_stats) */
+    VG_FLAG_LIT_INFLATE_AFTER_TRACE = 1u << 1,
+    VG_FLAG_LIT_SKIP_START_VOXEL = 1u << 2,
+    VG_FLAG_LIT_LOC_OCCUPANCY = 1u << 3
 };
 
 /*
@@ -378,7 +399,8 @@ enum {
     VG_K_RAYTRACE = 2, /* K3 */
     VG_K_MERGE = 3,    /* K4 */
     VG_K_SHIFT = 4,    /* K5 */
-    VG_NKERNELS = 5
+    VG_K_LOC_OCCUPANCY = 5, /* loc_grid's occupied voxels as a bit plane (VG_FLAG_LIT_LOC_OCCUPANCY) */
+    VG_NKERNELS = 6
 };
 
 /*

@@ -6,20 +6,46 @@
 namespace vg {
 namespace {
 
-template <bool ALIGN8>
+template <bool ALIGN8, bool RL>
 __global__ void __launch_bounds__(256) k_merge(const PlaneGeom g, Planes pl, uint8_t *__restrict__ loc) {
     pdl_trigger();
     pdl_wait();
-    units::merge_word<ALIGN8, units::LoadPlain>(g, pl, loc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    units::merge_word<ALIGN8, units::LoadPlain, RL>(g, pl, loc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+template <bool RL>
 __global__ void __launch_bounds__(256) k_merge_shift(const PlaneGeom g, Planes pl, const uint8_t *__restrict__ src,
                                                      uint8_t *__restrict__ dst, const int32_t dx, const int32_t dy,
                                                      const int32_t dz) {
     __shared__ __align__(16) uint8_t sm[units::kMergeShiftSmem];
     pdl_trigger();
     pdl_wait();
-    units::merge_shift_unit<units::LoadRO, units::LoadPlain>(g, pl, src, dst, dx, dy, dz, blockIdx.x, sm);
+    units::merge_shift_unit<units::LoadRO, units::LoadPlain, RL>(g, pl, src, dst, dx, dy, dz, blockIdx.x, sm);
+}
+
+// The literal loc_grid reading of Alg. 2: the occupied voxels of loc_grid,
+// after a pending re-centre by (dx, dy, dz), as a bit plane (one thread per
+// plane word, every word written).
+__global__ void __launch_bounds__(256) k_loc_occupancy(const PlaneGeom g, const uint8_t *__restrict__ loc,
+                                                       const int32_t dx, const int32_t dy, const int32_t dz,
+                                                       uint32_t *__restrict__ out) {
+    pdl_trigger();
+    pdl_wait();
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= g.words) return;
+    const int32_t x0 = (int32_t)(w % g.wx) * 32;
+    const int64_t row = w / g.wx;
+    const int32_t sy = (int32_t)(row % g.ny) + dy, sz = (int32_t)(row / g.ny) + dz;
+    uint32_t bits = 0;
+    if (x0 < g.nx && (unsigned)sy < (unsigned)g.ny && (unsigned)sz < (unsigned)g.nz) {
+        const uint8_t *src = loc + ((int64_t)sz * g.ny + sy) * g.nx;
+        const int nbits = min(32, g.nx - x0);
+        for (int k = 0; k < nbits; ++k) {
+            const int32_t sx = x0 + k + dx;
+            if ((unsigned)sx < (unsigned)g.nx && __ldg(src + sx) == 2) bits |= 1u << k;   // VG_OCC
+        }
+    }
+    out[w] = bits;
 }
 
 __global__ void __launch_bounds__(256) k_shift(const PlaneGeom g, const int32_t dx, const int32_t dy,
@@ -36,16 +62,30 @@ cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s) {
     const unsigned blocks = (unsigned)((a.g.words + 255) / 256);
     if (blocks == 0) return cudaSuccess;
     // 8-byte loc stores need 8-byte aligned rows and buffer
-    if (a.g.nx % 8 == 0 && reinterpret_cast<uintptr_t>(a.loc) % 8 == 0)
-        return launch_pdl(k_merge<true>, blocks, 256, 0, s, a.g, a.pl, a.loc);
-    return launch_pdl(k_merge<false>, blocks, 256, 0, s, a.g, a.pl, a.loc);
+    const bool a8 = a.g.nx % 8 == 0 && reinterpret_cast<uintptr_t>(a.loc) % 8 == 0;
+    if (a.lit & kLitRaysLast) {
+        if (a8) return launch_pdl(k_merge<true, true>, blocks, 256, 0, s, a.g, a.pl, a.loc);
+        return launch_pdl(k_merge<false, true>, blocks, 256, 0, s, a.g, a.pl, a.loc);
+    }
+    if (a8) return launch_pdl(k_merge<true, false>, blocks, 256, 0, s, a.g, a.pl, a.loc);
+    return launch_pdl(k_merge<false, false>, blocks, 256, 0, s, a.g, a.pl, a.loc);
 }
 
 cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s) {
     const unsigned blocks = (unsigned)units::merge_shift_units(a.g);
     if (blocks == 0) return cudaSuccess;
-    return launch_pdl(k_merge_shift, blocks, 256, 0, s, a.g, a.pl, (const uint8_t *)a.loc, dst, delta[0], delta[1],
-                      delta[2]);
+    if (a.lit & kLitRaysLast)
+        return launch_pdl(k_merge_shift<true>, blocks, 256, 0, s, a.g, a.pl, (const uint8_t *)a.loc, dst, delta[0],
+                          delta[1], delta[2]);
+    return launch_pdl(k_merge_shift<false>, blocks, 256, 0, s, a.g, a.pl, (const uint8_t *)a.loc, dst, delta[0],
+                      delta[1], delta[2]);
+}
+
+cudaError_t launch_loc_occupancy(const PlaneGeom &g, const uint8_t *loc, const int32_t delta[3], uint32_t *out,
+                                 cudaStream_t s) {
+    const unsigned blocks = (unsigned)((g.words + 255) / 256);
+    if (blocks == 0) return cudaSuccess;
+    return launch_pdl(k_loc_occupancy, blocks, 256, 0, s, g, loc, delta[0], delta[1], delta[2], out);
 }
 
 cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8_t *src, uint8_t *dst,

@@ -8,7 +8,7 @@ namespace {
 
 using namespace rt;
 
-template <int LPR>
+template <int LPR, bool EXACT>
 __global__ void __launch_bounds__(kThreads, 5) k_raytrace(const FrameArgs a, const int buffered) {
     __shared__ uint32_t box_fr[kBoxWords], box_tr[kBoxWords], occ_box[kBoxWords];
     extern __shared__ uint32_t buf[];   // kRtBuf * kThreads, one column per thread
@@ -25,9 +25,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_raytrace(const FrameArgs a, con
     rt_setup<LPR>(a, S, blockIdx.x, ln);
     pdl_wait();
     box_stage<units::LoadRO>(a, b, box_fr, box_tr, occ_box);
-    unsigned visits = rt_walk<LPR, units::LoadRO>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
+    unsigned visits = rt_walk<LPR, units::LoadRO, EXACT>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
     for (int64_t grp = blockIdx.x + gridDim.x; grp < groups; grp += gridDim.x)
-        visits += rt_group<LPR, units::LoadRO>(a, S, b, grp, buffered, box_fr, box_tr, occ_box, buf);
+        visits += rt_group<LPR, units::LoadRO, EXACT>(a, S, b, grp, buffered, box_fr, box_tr, occ_box, buf);
     box_flush(a, b, box_fr, box_tr);
     if (a.stats) {
         const unsigned total = __reduce_add_sync(kFull, visits);
@@ -41,10 +41,14 @@ int g_blocks_per_sm[64][6];
 template <int LPR>
 cudaError_t configure_lpr(int dev, int idx) {
     const size_t dyn = sizeof(uint32_t) * kRtBuf * kThreads;
-    cudaError_t e = cudaFuncSetAttribute(k_raytrace<LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaError_t e = cudaFuncSetAttribute(k_raytrace<LPR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_raytrace<LPR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_blocks_per_sm[dev][idx], k_raytrace<LPR>, kThreads,
-                                                         dyn);
+    // the exact variant is sized like the default one (same bounds and buffer)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_blocks_per_sm[dev][idx], k_raytrace<LPR, false>,
+                                                         kThreads, dyn);
 }
 
 template <int LPR>
@@ -59,7 +63,11 @@ cudaError_t launch_lpr(const FrameArgs &a, int idx, cudaStream_t s) {
     if (blocks == 0) return cudaSuccess;
     // a packed visit holds a plane bit index below 2^31
     const int buffered = a.g.words < (int64_t(1) << 26) ? 1 : 0;
-    return launch_pdl(k_raytrace<LPR>, blocks, kThreads, sizeof(uint32_t) * kRtBuf * kThreads, s, a, buffered);
+    const size_t dyn = sizeof(uint32_t) * kRtBuf * kThreads;
+    // traced marks must skip tested-occupied voxels only when the tested
+    // plane is not covered by occ_inf (the literal loc_grid reading)
+    if (a.lit & kLitRaysLast) return launch_pdl(k_raytrace<LPR, true>, blocks, kThreads, dyn, s, a, buffered);
+    return launch_pdl(k_raytrace<LPR, false>, blocks, kThreads, dyn, s, a, buffered);
 }
 
 }  // namespace
@@ -85,7 +93,9 @@ int auto_lanes_per_ray(int32_t vd, int32_t hw, int32_t hh) {
     return 32;
 }
 
-cudaError_t launch_raytrace(const FrameArgs &a, int lanes_per_ray, cudaStream_t s) {
+cudaError_t launch_raytrace(const FrameArgs &a_in, int lanes_per_ray, cudaStream_t s) {
+    FrameArgs a = a_in;
+    if (!a.occ_test) a.occ_test = a.pl.occ_inf;   // the default reading: rays test the inflated plane
     switch (lanes_per_ray) {
     case 1: return launch_lpr<1>(a, 0, s);
     case 2: return launch_lpr<2>(a, 1, s);

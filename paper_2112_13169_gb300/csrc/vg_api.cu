@@ -43,6 +43,7 @@ struct vg_grid {
     bool pend_on;
     int32_t pend[3];
     vg::Planes pl;
+    uint32_t *loc_occ;    // VG_FLAG_LIT_LOC_OCCUPANCY: the plane its rays test
     unsigned long long *stats;
     void *staging;        // device copy of host inputs
     size_t staging_bytes;
@@ -94,6 +95,9 @@ bool position_ok(const vg_params *p, const double pos[3]) {
     return true;
 }
 
+constexpr uint32_t kLitFlags =
+    VG_FLAG_LIT_INFLATE_AFTER_TRACE | VG_FLAG_LIT_SKIP_START_VOXEL | VG_FLAG_LIT_LOC_OCCUPANCY;
+
 bool params_ok(const vg_params *p) {
     if (!p) return false;
     int64_t nv = 1;
@@ -107,6 +111,8 @@ bool params_ok(const vg_params *p) {
     if (!(p->fov_y_deg > 0.0f && p->fov_y_deg < 180.0f)) return false;
     if (!(std::isfinite(p->depth) && p->depth > 0.0f)) return false;
     if (p->vox_inf < 0 || p->vox_inf > vg::kMaxInflate) return false;
+    if (p->flags & ~(VG_FLAG_STATS | kLitFlags)) return false;
+    if ((p->flags & VG_FLAG_LIT_INFLATE_AFTER_TRACE) && (p->flags & VG_FLAG_LIT_LOC_OCCUPANCY)) return false;
     const double vd = (double)p->depth / (double)p->vox_size;
     if (!(vd < 1.0e6)) return false;
     return true;
@@ -128,10 +134,10 @@ PlaneGeom geom_of(const vg_params *p) {
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t loc, loc_alt, occ_raw, occ_inf, fr, tr, stats, total;
+    size_t loc, loc_alt, occ_raw, occ_inf, fr, tr, loc_occ, stats, total;
 };
 
-Layout layout_of(const PlaneGeom &g) {
+Layout layout_of(const PlaneGeom &g, uint32_t flags) {
     Layout L;
     size_t off = 0;
     // 16 bytes of slack after each loc buffer: K5's vector path may read up
@@ -143,6 +149,8 @@ Layout layout_of(const PlaneGeom &g) {
     L.occ_inf = off; off += planeb;
     L.fr = off; off += planeb;
     L.tr = off; off += planeb;
+    L.loc_occ = off;   // only for the literal loc_grid reading
+    if (flags & VG_FLAG_LIT_LOC_OCCUPANCY) off += planeb;
     L.stats = off; off += 256;
     L.total = off;
     return L;
@@ -256,6 +264,8 @@ FrameArgs frame_args(vg_grid *G, const vg::Pose32 &T) {
     a.pl = G->pl;
     a.loc = G->loc;
     a.stats = (G->p.flags & VG_FLAG_STATS) ? G->stats : nullptr;
+    a.lit = ((G->p.flags & VG_FLAG_LIT_SKIP_START_VOXEL) ? vg::kLitSkipStart : 0) |
+            ((G->p.flags & VG_FLAG_LIT_LOC_OCCUPANCY) ? vg::kLitRaysLast : 0);
     return a;
 }
 
@@ -310,6 +320,18 @@ cudaError_t finish_frame(vg_grid *G, FrameArgs &a, cudaStream_t s) {
     } else {
         a.pl.occ_inf = a.pl.occ_raw;   // no inflation: the raw plane is the inflated one
     }
+    // the plane the rays test: the inflated one (Alg. 1's order), or a
+    // literal reading's
+    a.occ_test = a.pl.occ_inf;
+    if (G->p.flags & VG_FLAG_LIT_INFLATE_AFTER_TRACE) a.occ_test = a.pl.occ_raw;
+    if (G->p.flags & VG_FLAG_LIT_LOC_OCCUPANCY) {
+        const int32_t none[3] = {0, 0, 0};
+        e = launch(G, VG_K_LOC_OCCUPANCY, s, [&] {
+            return vg::launch_loc_occupancy(G->g, G->loc, G->pend_on ? G->pend : none, G->loc_occ, s);
+        });
+        if (e != cudaSuccess) return e;
+        a.occ_test = G->loc_occ;
+    }
     const int lpr = G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh);
     e = launch(G, VG_K_RAYTRACE, s, [&] { return vg::launch_raytrace(a, lpr, s); });
     if (e != cudaSuccess) return e;
@@ -342,7 +364,7 @@ const char *vg_strerror(int status) {
 
 int64_t vg_grid_bytes(const vg_params *params) {
     if (!params_ok(params)) return 0;
-    return (int64_t)layout_of(geom_of(params)).total;
+    return (int64_t)layout_of(geom_of(params), params->flags).total;
 }
 
 int64_t vg_ray_bundle(const vg_params *params, int32_t out[3]) {
@@ -364,7 +386,7 @@ int vg_create(const vg_params *params, const double robot_pos_w[3], void *stream
     G->lanes_per_ray = 0;   // automatic
     cudaError_t e = cudaGetDevice(&G->device);
     if (e == cudaSuccess) e = configure_device(G->device);
-    const Layout L = layout_of(G->g);
+    const Layout L = layout_of(G->g, params->flags);
     if (e == cudaSuccess) e = cudaMalloc((void **)&G->base, L.total);
     if (e != cudaSuccess) {
         delete G;
@@ -376,6 +398,8 @@ int vg_create(const vg_params *params, const double robot_pos_w[3], void *stream
     G->pl.occ_inf = reinterpret_cast<uint32_t *>(G->base + L.occ_inf);
     G->pl.fr = reinterpret_cast<uint32_t *>(G->base + L.fr);
     G->pl.tr = reinterpret_cast<uint32_t *>(G->base + L.tr);
+    G->loc_occ = (params->flags & VG_FLAG_LIT_LOC_OCCUPANCY) ? reinterpret_cast<uint32_t *>(G->base + L.loc_occ)
+                                                              : nullptr;
     G->stats = reinterpret_cast<unsigned long long *>(G->base + L.stats);
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(G->base, 0, L.total, s);   // VG_UNK == 0, planes empty
@@ -425,8 +449,8 @@ int vg_profile_read(vg_grid *G, double ms[VG_NKERNELS], int64_t timed[VG_NKERNEL
     if (!G) return VG_EINVAL;
     DeviceGuard dg(G->device);
     if (!dg.ok) return VG_ECUDA;
-    double acc[VG_NKERNELS] = {0, 0, 0, 0, 0};
-    int64_t cnt[VG_NKERNELS] = {0, 0, 0, 0, 0};
+    double acc[VG_NKERNELS] = {};
+    int64_t cnt[VG_NKERNELS] = {};
     if (G->prof_used) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return status_of(e);
@@ -635,7 +659,7 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
         if ((int64_t)f.width * f.height >= (int64_t(1) << 31)) return VG_EINVAL;
         if (f.dtype != VG_DEPTH_F32 && f.dtype != VG_DEPTH_U16) return VG_EINVAL;
         if (f.dtype == VG_DEPTH_U16 && !(std::isfinite(f.depth_scale) && f.depth_scale > 0.0f)) return VG_EINVAL;
-        if (G->device != B->device || G->p.vox_inf > 3) return VG_EINVAL;
+        if (G->device != B->device || G->p.vox_inf > 3 || (G->p.flags & kLitFlags)) return VG_EINVAL;
         if (f.recentre && !position_ok(&G->p, f.robot_pos_w)) return VG_EINVAL;
         vg::Pose32 T;
         if (!pose_of(G, f.T_wc, T)) return VG_EINVAL;
@@ -662,6 +686,7 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
         std::memset(&it, 0, sizeof(it));
         it.a = depth_frame_args(G, T, f.depth, f.width, f.height, f.dtype, f.depth_scale);
         if (G->p.vox_inf == 0) it.a.pl.occ_inf = it.a.pl.occ_raw;
+        it.a.occ_test = it.a.pl.occ_inf;
         it.dtype = f.dtype;
         it.vec = (reinterpret_cast<uintptr_t>(f.depth) % (f.dtype == VG_DEPTH_F32 ? 16 : 8)) == 0;
         int lpr = B->lanes ? B->lanes : (G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh));

@@ -91,7 +91,13 @@ struct FrameArgs {
     Planes pl;
     uint8_t *loc;
     unsigned long long *stats;  // NULL unless VG_FLAG_STATS
+    // literal readings (comparison flags; 0 for the default reading)
+    const uint32_t *occ_test;   // the plane K3's rays test; NULL: pl.occ_inf
+    int32_t lit;                // kLit* bits
 };
+
+constexpr int32_t kLitSkipStart = 1;    // rays do not visit their start voxel
+constexpr int32_t kLitRaysLast = 2;     // resolve: free > traced > occupied
 
 // One frame of a batch (k_batch.cu): its FrameArgs plus the layout of its
 // units in each phase.
@@ -142,6 +148,9 @@ cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s);
 cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s);
 cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8_t *src,
                          uint8_t *dst, cudaStream_t s);
+// loc_grid's occupied voxels after a re-centre by delta, as a bit plane
+cudaError_t launch_loc_occupancy(const PlaneGeom &g, const uint8_t *loc, const int32_t delta[3], uint32_t *out,
+                                 cudaStream_t s);
 cudaError_t configure_batch(int dev);   // once per device, before the first launch_batch
 int batch_max_blocks(int dev);          // CTAs of k_batch resident at once on the device
 cudaError_t launch_batch(const BatchItem *items, BatchCtl *ctl, int blocks, cudaStream_t s);

@@ -19,8 +19,10 @@
 // quotient 1/D_k; the face coordinate is kept as an exact float.
 //
 // Free-space rule (Alg. 2): voxels before the ray's first occupied voxel
-// (of the inflated plane) are marked free, voxels after it
-// unknown-and-traced; occupied voxels are never marked free.  The paper's
+// (of the inflated plane; a.occ_test, which a literal reading may point
+// elsewhere) are marked free, voxels after it unknown-and-traced; occupied
+// voxels are never marked free.  With kLitSkipStart the walk moves before
+// its first visit, so the start voxel is left out.  The paper's
 // racy single-grid writes are replaced by two bit planes, fr and tr, merged
 // by K4 with precedence occupied > free > traced, so the result does not
 // depend on the order rays run in.
@@ -175,7 +177,7 @@ __device__ __forceinline__ uint32_t pack_visit(const Walker &w, const Box &b) {
 
 template <class L>
 __device__ __forceinline__ uint32_t occ_word(const FrameArgs &a, const uint32_t *occ_box, uint32_t p) {
-    return (p & kBoxFlag) ? occ_box[(p >> 5) & (kBoxWords - 1)] : L::ld(a.pl.occ_inf + (p >> 5));
+    return (p & kBoxFlag) ? occ_box[(p >> 5) & (kBoxWords - 1)] : L::ld(a.occ_test + (p >> 5));
 }
 
 // Pending marks of one lane: consecutive marks of the same word and kind
@@ -245,10 +247,12 @@ __device__ int walk_first_hit(const FrameArgs &a, const Ray &r, const int32_t n0
     return -1;
 }
 
-// Pass 2 of the two-pass walk: marks the slice's in-grid visits.
+// Pass 2 of the two-pass walk: marks the slice's in-grid visits.  EXACT:
+// traced marks skip voxels the rays test as occupied (see rt_walk).
+template <bool EXACT, class L>
 __device__ inline unsigned walk_marks(const FrameArgs &a, const Ray &r, const int32_t n0[3], bool visit_start,
                                float c_hi, const Box &b, int mode, int32_t hit_at, uint32_t *box_fr,
-                               uint32_t *box_tr, uint32_t R) {
+                               uint32_t *box_tr, const uint32_t *occ_box, uint32_t R) {
     Walker w;
     walker_init(w, r, n0, R);
     bool more = visit_start ? true : walker_next(w, r, c_hi);
@@ -257,8 +261,11 @@ __device__ inline unsigned walk_marks(const FrameArgs &a, const Ray &r, const in
     while (more) {
         if (in_grid(w, r)) {
             // mode: 0 all free, 1 free before hit_at and traced after, 2 all traced
-            if (!(mode == 1 && q == hit_at))
-                marks_add(a, box_fr, box_tr, m, pack_visit(w, b), mode == 2 || (mode == 1 && q > hit_at));
+            const bool traced = mode == 2 || (mode == 1 && q > hit_at);
+            const uint32_t p = pack_visit(w, b);
+            bool skip = mode == 1 && q == hit_at;
+            if (EXACT && traced && !skip) skip = (occ_word<L>(a, occ_box, p) >> (p & 31u)) & 1u;
+            if (!skip) marks_add(a, box_fr, box_tr, m, p, traced);
             ++q;
         } else if (gone(w, r)) {
             break;
@@ -291,7 +298,7 @@ __device__ __forceinline__ void box_stage(const FrameArgs &a, const Box &b, uint
         const int32_t wx = b.bw0 + dw, y = b.by0 + dy, z = b.bz0 + dz;
         uint32_t v = 0;
         if (wx >= 0 && wx < a.g.wx && y >= 0 && y < a.g.ny && z >= 0 && z < a.g.nz)
-            v = L::ld(a.pl.occ_inf + ((uint32_t)z * (uint32_t)a.g.ny + (uint32_t)y) * (uint32_t)a.g.wx + wx);
+            v = L::ld(a.occ_test + ((uint32_t)z * (uint32_t)a.g.ny + (uint32_t)y) * (uint32_t)a.g.wx + wx);
         occ_box[i] = v;
     }
     __syncthreads();
@@ -407,7 +414,13 @@ __device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], i
 // CTA; `buf` is this CTA's visit buffer (kRtBuf columns of kThreads words).
 // Returns this thread's in-grid visits.  Warp-synchronous (every lane of
 // every warp must call it; the CTA need not be in step).
-template <int LPR, class L>
+// Traced marks after a ray's first occupied voxel are written without
+// re-reading the occupancy; a traced mark on an occupied voxel is then
+// overridden by K4's precedence.  That holds whenever the tested plane is a
+// subset of occ_inf; for a tested plane that is not (the literal loc_grid
+// reading, whose resolve also puts traced above occupied) EXACT re-reads it
+// and leaves tested-occupied voxels unmarked, as Alg. 2 does.
+template <int LPR, class L, bool EXACT = false>
 __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, const Box &b, int buffered,
                                             uint32_t *box_fr, uint32_t *box_tr, const uint32_t *occ_box,
                                             uint32_t *buf) {
@@ -426,7 +439,7 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
     if (active && !ovf) {
         Walker w;
         walker_init(w, r, n0, R);
-        bool more = (j == 0) ? true : walker_next(w, r, c_hi);
+        bool more = (j == 0 && !(a.lit & kLitSkipStart)) ? true : walker_next(w, r, c_hi);
         while (more) {
             if (in_grid(w, r)) {
                 if (nvis == kRtBuf) {
@@ -452,7 +465,8 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
                 if (q0 + c < nvis && ((v[c] >> (p[c] & 31u)) & 1u)) hit_at = q0 + c;
         }
     }
-    if (active && ovf) hit_at = walk_first_hit<L>(a, r, n0, j == 0, c_hi, b, occ_box, R);
+    const bool visit_start = j == 0 && !(a.lit & kLitSkipStart);
+    if (active && ovf) hit_at = walk_first_hit<L>(a, r, n0, visit_start, c_hi, b, occ_box, R);
 
     // ---- first lane of this ray with an occupied voxel ---------------
     const unsigned hits = __ballot_sync(kFull, hit_at >= 0);
@@ -467,25 +481,27 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
         Marks m;
         for (int q = 0; q < nvis; ++q) {
             if (mode == 1 && q == hit_at) continue;
-            marks_add(a, box_fr, box_tr, m, buf[q * kThreads + threadIdx.x],
-                      mode == 2 || (mode == 1 && q > hit_at));
+            const bool traced = mode == 2 || (mode == 1 && q > hit_at);
+            const uint32_t p = buf[q * kThreads + threadIdx.x];
+            if (EXACT && traced && ((occ_word<L>(a, occ_box, p) >> (p & 31u)) & 1u)) continue;
+            marks_add(a, box_fr, box_tr, m, p, traced);
         }
         marks_flush(a, box_fr, box_tr, m);
         visits += (unsigned)nvis;
     } else if (active) {
-        visits += walk_marks(a, r, n0, j == 0, c_hi, b, mode, hit_at, box_fr, box_tr, R);
+        visits += walk_marks<EXACT, L>(a, r, n0, visit_start, c_hi, b, mode, hit_at, box_fr, box_tr, occ_box, R);
     }
     return visits;
 }
 
 // One group of rays: rt_setup then rt_walk.
-template <int LPR, class L>
+template <int LPR, class L, bool EXACT = false>
 __device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3], const Box &b, int64_t group,
                                              int buffered, uint32_t *box_fr, uint32_t *box_tr,
                                              const uint32_t *occ_box, uint32_t *buf) {
     Lane ln;
     rt_setup<LPR>(a, S, group, ln);
-    return rt_walk<LPR, L>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
+    return rt_walk<LPR, L, EXACT>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
 }
 
 }  // namespace rt

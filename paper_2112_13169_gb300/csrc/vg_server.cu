@@ -300,6 +300,8 @@ void vg_server_destroy(vg_server *S) {
 
 int vg_server_add_camera(vg_server *S, const vg_params *params, const double robot_pos_w[3], int32_t *camera) {
     if (!S || !params || !robot_pos_w || !camera || params->vox_inf > 3) return VG_EINVAL;
+    if (params->flags & (VG_FLAG_LIT_INFLATE_AFTER_TRACE | VG_FLAG_LIT_SKIP_START_VOXEL | VG_FLAG_LIT_LOC_OCCUPANCY))
+        return VG_EINVAL;   // literal readings take the plain path only
     const int64_t bytes = vg_grid_bytes(params);
     if (bytes <= 0) return VG_EINVAL;
     {

@@ -275,14 +275,18 @@ __device__ __forceinline__ void inflate_tile(const PlaneGeom &g, const uint32_t 
 // leaves all planes zero for the next frame (occ_raw is a subset of occ_inf,
 // so its non-zero words are cleared too).
 // ---------------------------------------------------------------------------
+// RAYS_LAST: the literal loc_grid reading, in which the rays' marks replace
+// the measurement's occupied marks (free > traced > occupied).
+template <bool RAYS_LAST = false>
 __device__ __forceinline__ uint8_t resolve(uint32_t oc, uint32_t f, uint32_t t, int b, uint8_t old) {
-    if ((oc >> b) & 1u) return 2;   // VG_OCC
-    if ((f >> b) & 1u) return 1;    // VG_FREE
-    if ((t >> b) & 1u) return 3;    // VG_TRACED
+    if (!RAYS_LAST && ((oc >> b) & 1u)) return 2;   // VG_OCC
+    if ((f >> b) & 1u) return 1;                    // VG_FREE
+    if ((t >> b) & 1u) return 3;                    // VG_TRACED
+    if (RAYS_LAST && ((oc >> b) & 1u)) return 2;
     return old;
 }
 
-template <bool ALIGN8, class L>
+template <bool ALIGN8, class L, bool RAYS_LAST = false>
 __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl, uint8_t *loc, int64_t w) {
     if (w >= g.words) return;
     const int32_t wxi = (int32_t)(w % g.wx);
@@ -306,12 +310,12 @@ __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl,
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
                 const uint8_t ob = (uint8_t)(old >> (8 * b));
-                v |= (uint64_t)resolve(oc, f, t, 8 * c + b, ob) << (8 * b);
+                v |= (uint64_t)resolve<RAYS_LAST>(oc, f, t, 8 * c + b, ob) << (8 * b);
             }
             *p = v;
         } else {
             for (int b = 8 * c; b < 8 * c + 8 && b < nbits; ++b)
-                if ((any >> b) & 1u) Lp[b] = resolve(oc, f, t, b, 0);
+                if ((any >> b) & 1u) Lp[b] = resolve<RAYS_LAST>(oc, f, t, b, 0);
         }
     }
     if (oc) {
@@ -340,7 +344,7 @@ __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl,
 // launch), LP the planes (cleared by the launch).
 constexpr int kMergeShiftSmem = 8192 + 64;
 
-template <class LS, class LP>
+template <class LS, class LP, bool RAYS_LAST = false>
 __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Planes &pl, const uint8_t *src,
                                                  uint8_t *dst, int32_t dx, int32_t dy, int32_t dz, int64_t u,
                                                  uint8_t *sm) {
@@ -417,7 +421,7 @@ __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Plane
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int k = 4 * m + b;
-                v |= (uint32_t)resolve(oc, f, t, k, (uint8_t)(old[m] >> (8 * b))) << (8 * b);
+                v |= (uint32_t)resolve<RAYS_LAST>(oc, f, t, k, (uint8_t)(old[m] >> (8 * b))) << (8 * b);
             }
             nv[m] = v;
         }

@@ -21,6 +21,9 @@ VG_UNK, VG_FREE, VG_OCC, VG_TRACED = range(4)
 VG_DEPTH_F32, VG_DEPTH_U16 = 0, 1
 VG_MEM_DEVICE, VG_MEM_HOST = 0, 1
 VG_FLAG_STATS = 1
+VG_FLAG_LIT_INFLATE_AFTER_TRACE = 2
+VG_FLAG_LIT_SKIP_START_VOXEL = 4
+VG_FLAG_LIT_LOC_OCCUPANCY = 8
 
 # every symbol include/vg.h declares
 EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points", "vg_shift",
@@ -31,7 +34,7 @@ EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points
            "vg_server_add_camera", "vg_server_remove_camera", "vg_server_submit", "vg_server_wait",
            "vg_server_read", "vg_server_stats")
 VG_TUNE_BATCH_CTAS_PER_SM, VG_TUNE_BATCH_LANES = 100, 101
-KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift")
+KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift", "loc_occupancy")
 VG_TUNE_RT_LANES = 0
 
 
@@ -294,9 +297,10 @@ def vg_profile_enable(h, enable=True):
 
 def vg_profile_read(h, reset=True):
     """{kernel: (summed ms, timed launches, total launches)}; synchronises."""
-    ms = (C.c_double * 5)()
-    timed = (C.c_int64 * 5)()
-    total = (C.c_int64 * 5)()
+    nk = len(KERNELS)   # VG_NKERNELS
+    ms = (C.c_double * nk)()
+    timed = (C.c_int64 * nk)()
+    total = (C.c_int64 * nk)()
     _check(load().vg_profile_read(h, ms, timed, total, 1 if reset else 0), "vg_profile_read")
     return {k: (ms[i], timed[i], total[i]) for i, k in enumerate(KERNELS)}
 

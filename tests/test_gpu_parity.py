@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from oracle import OracleGrid, OracleParams
+from oracle.oracle import LIT_INFLATE_AFTER_TRACE, LIT_LOC_OCCUPANCY, LIT_SKIP_START
 from synth import body_pose, make
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +48,10 @@ class Pair:
         self.g = vg.Grid(n, vs, fx, fy, depth, r, pos, flags=flags)
         if lanes:
             self.g.tune(lanes)
-        self.o = OracleGrid(OracleParams(tuple(n), vs, fx, fy, depth, r), pos)
+        lit = ((LIT_INFLATE_AFTER_TRACE if flags & vg.VG_FLAG_LIT_INFLATE_AFTER_TRACE else 0) |
+               (LIT_SKIP_START if flags & vg.VG_FLAG_LIT_SKIP_START_VOXEL else 0) |
+               (LIT_LOC_OCCUPANCY if flags & vg.VG_FLAG_LIT_LOC_OCCUPANCY else 0))
+        self.o = OracleGrid(OracleParams(tuple(n), vs, fx, fy, depth, r, lit), pos)
         self.out = torch.empty(self.g.nvox, dtype=torch.uint8, device="cuda")
 
     def depth(self, d, T, scale=1.0, device=True, check=True):
@@ -84,14 +88,14 @@ class Pair:
         self.g.close()
 
 
-def run_workload(vg, w, nframes, lanes=None, device=True, shift=True):
+def run_workload(vg, w, nframes, lanes=None, device=True, shift=True, flags=0):
     """Frames with a re-centre after each.  A grid is read (and compared)
     after every frame but not after its re-centre, so the re-centre is
     still pending when the next frame comes and that frame's merge applies
     it; the last re-centre is applied on its own by the final read."""
     g = w.grid
     f0 = w.frames[0]
-    P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, f0.robot_pos, lanes)
+    P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, f0.robot_pos, lanes, flags=flags)
     try:
         for i in range(nframes):
             f = w.frames[i]
@@ -395,3 +399,40 @@ def test_bad_arguments_on_device(vg):
     with pytest.raises(vg.VGError):
         P.g.shift((1e12, 0.0, 0.0))     # origin index beyond int32
     P.close()
+
+
+# --------------------------------------------------------------------------
+# literal readings (comparison flags): the same bit-exact bar
+
+
+LIT = {"inflate_after_trace": "VG_FLAG_LIT_INFLATE_AFTER_TRACE", "skip_start": "VG_FLAG_LIT_SKIP_START_VOXEL",
+       "loc_occupancy": "VG_FLAG_LIT_LOC_OCCUPANCY"}
+
+
+@pytest.mark.parametrize("lit", sorted(LIT))
+@pytest.mark.parametrize("name,frames", [("room", 1), ("paper", 3), ("robot", 4)])
+def test_literal_readings(vg, lit, name, frames):
+    # the robot sequences re-centre every frame, so the loc_grid reading
+    # also reads the grid through a pending re-centre
+    w = make(name, frames=frames, robot=3) if name == "robot" else make(name, frames=frames)
+    run_workload(vg, w, frames, flags=getattr(vg, LIT[lit]))
+
+
+def test_literal_readings_full_size(vg):
+    w = make("seq", frames=3)
+    run_workload(vg, w, 3, flags=vg.VG_FLAG_LIT_SKIP_START_VOXEL | vg.VG_FLAG_LIT_LOC_OCCUPANCY)
+
+
+def test_literal_flags_rejected_where_unsupported(vg):
+    bad = vg.VG_FLAG_LIT_INFLATE_AFTER_TRACE | vg.VG_FLAG_LIT_LOC_OCCUPANCY
+    with pytest.raises(vg.VGError):
+        vg.Grid((20, 20, 10), 0.1, 87.0, 58.0, 3.0, 1, (0, 0, 0), flags=bad)
+    with pytest.raises(vg.VGError):
+        vg.Grid((20, 20, 10), 0.1, 87.0, 58.0, 3.0, 1, (0, 0, 0), flags=1 << 9)
+    g = vg.Grid((20, 20, 10), 0.1, 87.0, 58.0, 3.0, 1, (0, 0, 0), flags=vg.VG_FLAG_LIT_SKIP_START_VOXEL)
+    d = torch.ones((8, 8), dtype=torch.float32, device="cuda")
+    b = vg.Batch(1)
+    with pytest.raises(vg.VGError):
+        b.step([(g, d, np.eye(4), None)])     # batches take the default reading only
+    b.close()
+    g.close()

@@ -84,6 +84,30 @@ def test_grid_bytes(vg):
     assert vg.vg_grid_bytes(bad) == 0
 
 
+def test_kernel_ids_match_the_header(vg):
+    # the binding sizes vg_profile_read's arrays from its kernel list
+    hdr = open(os.path.join(ROOT, "include", "vg.h")).read()
+    ids = dict(re.findall(r"VG_K_(\w+) = (\d+)", hdr))
+    n = int(re.search(r"VG_NKERNELS = (\d+)", hdr).group(1))
+    assert n == len(vg.KERNELS) == len(ids)
+    assert sorted(int(v) for v in ids.values()) == list(range(n))
+    for name, v in ids.items():
+        assert vg.KERNELS[int(v)] == name.lower(), (name, v)
+
+
+def test_grid_bytes_of_literal_flags(vg):
+    args = ((200, 200, 100), 0.05, 87, 58, 5.0, 2)
+    base = vg.vg_grid_bytes(vg.make_params(*args))
+    # the loc_grid reading holds one more bit plane; the others none
+    assert vg.vg_grid_bytes(vg.make_params(*args, flags=vg.VG_FLAG_LIT_LOC_OCCUPANCY)) == base + 8 * 4 * 200 * 100
+    for f in (vg.VG_FLAG_LIT_INFLATE_AFTER_TRACE, vg.VG_FLAG_LIT_SKIP_START_VOXEL, vg.VG_FLAG_STATS):
+        assert vg.vg_grid_bytes(vg.make_params(*args, flags=f)) == base
+    # exclusive readings, and unknown bits, are invalid parameters
+    both = vg.VG_FLAG_LIT_INFLATE_AFTER_TRACE | vg.VG_FLAG_LIT_LOC_OCCUPANCY
+    assert vg.vg_grid_bytes(vg.make_params(*args, flags=both)) == 0
+    assert vg.vg_grid_bytes(vg.make_params(*args, flags=1 << 7)) == 0
+
+
 @pytest.mark.parametrize("field,value", [
     ("grid_size", (0, 10, 10)), ("vox_size", 0.0), ("vox_size", float("nan")), ("fov_x_deg", 180.0),
     ("fov_y_deg", 0.0), ("depth", -1.0), ("vox_inf", 16), ("vox_inf", -1), ("grid_size", (2048, 2048, 1024)),
