@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--serve-cameras", type=int, default=256, help="cameras of the served form (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="seconds of Poisson arrivals")
     ap.add_argument("--serve-rate", type=float, default=30.0, help="frames per second per camera")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the step benchmark: the paper's Fig. 4 sweeps (step time vs points, "
+                         "rays and voxels) on the GPU beside the single-core oracle")
     return ap.parse_args()
 
 
@@ -744,10 +747,130 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# the paper's sweeps (Fig. 4a-c)
+# ---------------------------------------------------------------------------
+def _kernel_us(vg, grid, feed, frames, flush, kinds):
+    """Average event time per frame of the named kernels over `frames` calls
+    of feed(grid, k), after three untimed ones; L2 flushed before each."""
+    import torch
+    for k in range(3):
+        feed(grid, k)
+    torch.cuda.synchronize()
+    grid.profile(True)
+    grid.profile_read(reset=True)
+    for k in range(frames):
+        flush.zero_()
+        feed(grid, k)
+    torch.cuda.synchronize()
+    prof = grid.profile_read(reset=True)
+    return sum(prof[kind][0] / max(1, prof[kind][1]) for kind in kinds) * 1e3
+
+
+def _cpu_us(fn, reps):
+    best = None
+    for _ in range(reps):
+        t = time.perf_counter()
+        fn()
+        dt = time.perf_counter() - t
+        best = dt if best is None else min(best, dt)
+    return best * 1e6
+
+
+def run_sweeps(args):
+    """Fig. 4a-c of the paper: the time of step 2 (populate occupied voxels:
+    K1 + K2), step 3 (ray-trace: K3) and step 4 (merge: K4) as the number of
+    points, rays and voxels grows, for the GPU kernels (CUDA events the
+    library records around each launch, L2 flushed before each frame) and
+    the oracle's steps on one host core (best of a few runs).  Standard
+    set-up of Sec. V unless swept: 320x240, fov 85x101, depth 6.5 m,
+    100x100x20 at 0.15 m, vox_inf 2."""
+    import torch
+    from paper_2112_13169_gb300 import vg
+    from oracle import OracleParams
+    from oracle import oracle as O
+    from synth import make
+    vg.load()
+    orc = O.default()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    w = make("paper", frames=1)
+    f = w.frames[0]
+    pos = f.robot_pos
+    std = dict(n=(100, 100, 20), vs=0.15, fx=85.0, fy=101.0, depth=6.5, r=2)
+    rng = np.random.default_rng(4)
+    out = {}
+
+    def grid(n, vs, fx, fy, depth, r):
+        return vg.Grid(n, vs, fx, fy, depth, r, pos)
+
+    def oparams(n, vs, fx, fy, depth, r):
+        return OracleParams(tuple(n), vs, fx, fy, depth, r)
+
+    # (a) populate occupied voxels vs obstacle points (a point cloud in the
+    # camera frame, uniform in the field of view up to the range)
+    rows = []
+    for npts in (1000, 5000, 20000, 100000, 300000, 1000000):
+        z = rng.uniform(0.3, std["depth"], npts)
+        tx, ty = np.tan(np.radians(std["fx"] / 2)), np.tan(np.radians(std["fy"] / 2))
+        xyz = np.stack([rng.uniform(-tx, tx, npts) * z, rng.uniform(-ty, ty, npts) * z, z], 1).astype(np.float32)
+        dev = torch.from_numpy(xyz).cuda()
+        g = grid(**std)
+        gpu = _kernel_us(vg, g, lambda gr, k: gr.integrate_points(dev, f.T_wc), 20, flush, ("voxelize", "inflate"))
+        g.close()
+        p = oparams(**std)
+        o = orc.origin(p, pos)
+        pose = orc.pose_vc(p, f.T_wc, o)
+        cpu = _cpu_us(lambda: orc.inflate(p, orc.voxelize_points(p, pose, xyz)[0]), 3)
+        rows.append({"points": npts, "gpu_us": gpu, "cpu_us": cpu, "cpu_over_gpu": cpu / gpu})
+    out["populate_vs_points"] = rows
+
+    # (b) ray-trace vs rays: the field of view sets the bundle (the same
+    # depth image, back-projected with each field of view's intrinsics)
+    rows = []
+    dev = torch.from_numpy(f.depth).cuda()
+    for fov in (40.0, 60.0, 85.0, 101.0, 120.0, 140.0):
+        cfg = dict(std, fx=fov, fy=fov)
+        g = grid(**cfg)
+        gpu = _kernel_us(vg, g, lambda gr, k: gr.integrate_depth(dev, f.T_wc), 20, flush, ("raytrace",))
+        g.close()
+        p = oparams(**cfg)
+        (vd, hw, hh), nrays = orc.ray_bundle(p)
+        o = orc.origin(p, pos)
+        pose = orc.pose_vc(p, f.T_wc, o)
+        occ_inf = orc.inflate(p, orc.voxelize_depth(p, pose, f.depth)[0])
+        cpu = _cpu_us(lambda: orc.raytrace(p, pose, occ_inf), 3)
+        rows.append({"fov_deg": fov, "rays": int(nrays), "gpu_us": gpu, "cpu_us": cpu, "cpu_over_gpu": cpu / gpu})
+    out["raytrace_vs_rays"] = rows
+
+    # (c) merge vs voxels in the grid (the standard frame, no re-centre)
+    rows = []
+    for n in ((40, 40, 15), (100, 100, 20), (150, 150, 30), (200, 200, 100), (400, 400, 120)):
+        cfg = dict(std, n=n)
+        g = grid(**cfg)
+        gpu = _kernel_us(vg, g, lambda gr, k: gr.integrate_depth(dev, f.T_wc), 20, flush, ("merge",))
+        g.close()
+        p = oparams(**cfg)
+        o = orc.origin(p, pos)
+        pose = orc.pose_vc(p, f.T_wc, o)
+        occ_inf = orc.inflate(p, orc.voxelize_depth(p, pose, f.depth)[0])
+        fr, tr, _ = orc.raytrace(p, pose, occ_inf)
+        loc = np.zeros(p.shape, np.uint8)
+        cpu = _cpu_us(lambda: orc.merge(orc.resolve(occ_inf, fr, tr), loc), 3)
+        nv = n[0] * n[1] * n[2]
+        rows.append({"voxels": nv, "gpu_us": gpu, "cpu_us": cpu, "cpu_over_gpu": cpu / gpu})
+    out["merge_vs_voxels"] = rows
+    print(json.dumps({"sweeps": out, "gpu": "GB300, one GPU; CUDA events around each launch",
+                      "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": "best of 3 runs per point"},
+                      "data": "synthetic: the paper workload's first frame, random frustum points"}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweeps(args)
     return run_ours(args)
 
 
