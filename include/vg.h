@@ -100,7 +100,9 @@ enum {
 
 /*
  * Table I parameters of one local grid.
- *  grid_size  voxels per axis (x, y, z), each >= 1, total < 2^31.  The paper
+ *  grid_size  voxels per axis (x, y, z), each >= 1, total < 2^31, and fewer
+ *             than 2^27 plane words (WX * Ny * Nz, WX = ceil(Nx/32) rounded up
+ *             to a power of two, at least 4; only Nx far below 32 nears it).  The paper
  *             gives sizes in metres (Sec. V); callers convert with
  *             round(m / vox_size).
  *  vox_size   voxel edge in metres, finite, > 0.

@@ -111,6 +111,13 @@ bool params_ok(const vg_params *p) {
     if (!(p->fov_y_deg > 0.0f && p->fov_y_deg < 180.0f)) return false;
     if (!(std::isfinite(p->depth) && p->depth > 0.0f)) return false;
     if (p->vox_inf < 0 || p->vox_inf > vg::kMaxInflate) return false;
+    // K3 indexes plane bits with 32 bits: at most 2^27 plane words (a grid
+    // under 2^31 voxels exceeds that only when Nx is far below 32)
+    {
+        int64_t w = (p->grid_size[0] + 31) / 32, wx = 4;
+        while (wx < w) wx *= 2;
+        if (wx * (int64_t)p->grid_size[1] * p->grid_size[2] >= (int64_t(1) << 27)) return false;
+    }
     if (p->flags & ~(VG_FLAG_STATS | kLitFlags)) return false;
     if ((p->flags & VG_FLAG_LIT_INFLATE_AFTER_TRACE) && (p->flags & VG_FLAG_LIT_LOC_OCCUPANCY)) return false;
     const double vd = (double)p->depth / (double)p->vox_size;

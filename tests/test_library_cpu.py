@@ -111,6 +111,7 @@ def test_grid_bytes_of_literal_flags(vg):
 @pytest.mark.parametrize("field,value", [
     ("grid_size", (0, 10, 10)), ("vox_size", 0.0), ("vox_size", float("nan")), ("fov_x_deg", 180.0),
     ("fov_y_deg", 0.0), ("depth", -1.0), ("vox_inf", 16), ("vox_inf", -1), ("grid_size", (2048, 2048, 1024)),
+    ("grid_size", (1, 65536, 512)),   # 2^27 plane words: beyond K3's 32-bit plane bit index
 ])
 def test_create_rejects_bad_params(vg, field, value):
     kw = dict(n=(10, 10, 10), vox_size=0.1, fov_x_deg=87, fov_y_deg=58, depth=4.0, vox_inf=1)
