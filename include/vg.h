@@ -155,10 +155,12 @@ VG_API void vg_destroy(vg_grid *grid);
  *  depth        W x H pixels, row-major, tightly packed.  dtype VG_DEPTH_F32
  *               (metres) or VG_DEPTH_U16 (metres = raw * depth_scale).
  *  mem          VG_MEM_DEVICE: depth is a device pointer, read in place.
- *               VG_MEM_HOST: depth is host memory; it is copied with
- *               cudaMemcpyAsync into a staging buffer the grid owns (grown
- *               on first use of a larger frame; pinned host memory makes the
- *               copy asynchronous).
+ *               VG_MEM_HOST: depth is host memory.  Page-locked memory
+ *               (cudaMallocHost, cudaHostAlloc, cudaHostRegister) is read in
+ *               place by K1 over the host link and must stay valid until
+ *               the work on stream completes; other host memory is copied
+ *               with cudaMemcpyAsync into a staging buffer the grid owns
+ *               (grown on first use of a larger frame).
  *  depth_scale  used for VG_DEPTH_U16 only; finite, > 0.
  *  T_wc         camera pose, see above; must be finite.
  * A pixel is valid iff its depth d is finite, > 0 and <= params.depth.  The
@@ -196,8 +198,11 @@ VG_API int vg_shift(vg_grid *grid, const double robot_pos_w[3], void *stream);
  * dst is valid once that work completes.  dst_mem is VG_MEM_DEVICE or
  * VG_MEM_HOST; dst_bytes must be >= Nx*Ny*Nz.  origin (may be NULL)
  * receives the grid origin (voxel index of voxel (0,0,0) in the world
- * lattice) as of this call.  A pending re-centre (vg_shift) is applied on
- * stream first.
+ * lattice) as of this call.  With a re-centre pending (vg_shift), dst
+ * receives the re-centred grid: K5 writes it on stream straight into dst
+ * when dst is device memory or page-locked host memory and 16-byte aligned,
+ * else through the grid's second buffer and a copy.  The grid's own state
+ * does not change (the next merge still applies the re-centre).
  * Errors: VG_EINVAL, VG_ECUDA.
  */
 VG_API int vg_read(vg_grid *grid, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes,

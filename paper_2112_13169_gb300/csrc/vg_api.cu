@@ -235,7 +235,25 @@ cudaError_t configure_device(int dev) {
     return g_config_err[dev];
 }
 
+// The address at which the device reads or writes host memory directly:
+// page-locked allocations (cudaMallocHost / cudaHostAlloc / registered),
+// which the GPU reaches in place over the host link.  NULL for other
+// memory, which must be copied through the DMA engines instead.
+void *mapped_host(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // not a CUDA-known pointer: clear the error
+        return nullptr;
+    }
+    return (at.type == cudaMemoryTypeHost) ? at.devicePointer : nullptr;
+}
+
 int stage_input(vg_grid *G, const void *src, size_t bytes, cudaStream_t s, const void **dev_ptr) {
+    // page-locked input is read in place by K1 (no staging copy)
+    if (const void *m = mapped_host(src)) {
+        *dev_ptr = m;
+        return VG_OK;
+    }
     if (bytes > G->staging_bytes) {
         // grow-only staging buffer; the old one may still be read by queued work
         if (G->staging) {
@@ -564,8 +582,23 @@ int vg_read(vg_grid *G, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes, int32_
     DeviceGuard dg(G->device);
     if (!dg.ok) return VG_ECUDA;
     const cudaMemcpyKind kind = dst_mem == VG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    cudaError_t e = apply_pending(G, (cudaStream_t)stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, G->loc, (size_t)G->g.nvox, kind, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (G->pend_on) {
+        // the re-centred grid, without applying the re-centre: K5 writes it
+        // straight into dst where the device can store there (device memory
+        // or page-locked host memory, 16-byte aligned), else into loc_alt
+        // and then copies; the next merge still applies the re-centre
+        uint8_t *ddst = dst_mem == VG_MEM_DEVICE ? dst : static_cast<uint8_t *>(mapped_host(dst));
+        if (ddst && reinterpret_cast<uintptr_t>(ddst) % 16 == 0) {
+            e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, G->pend, G->loc, ddst, s); });
+        } else {
+            e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, G->pend, G->loc, G->loc_alt, s); });
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst, G->loc_alt, (size_t)G->g.nvox, kind, s);
+        }
+    } else {
+        e = cudaMemcpyAsync(dst, G->loc, (size_t)G->g.nvox, kind, s);
+    }
     if (e != cudaSuccess) return status_of(e);
     if (origin) std::memcpy(origin, G->origin, sizeof(G->origin));
     return VG_OK;

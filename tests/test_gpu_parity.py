@@ -301,6 +301,54 @@ def test_shifts_in_a_row_do_not_compose(vg):
     P.close()
 
 
+def test_reads_of_a_pending_shift_leave_the_grid_alone(vg):
+    # a read with a re-centre pending writes the re-centred grid into dst:
+    # straight into device memory or page-locked host memory (aligned), or
+    # through the second buffer (unaligned device memory, pageable memory);
+    # none of them applies the re-centre, which the next merge still does
+    rng = np.random.default_rng(16)
+    P = _pair(vg, n=(45, 31, 10))
+    P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([0.1, 0.2, 0.3], 0.2))
+    P.shift([0.5, -0.3, 0.2], check=False)
+    want = P.o.loc.ravel()
+    n = P.g.nvox
+    dev = torch.empty(n + 16, dtype=torch.uint8, device="cuda")
+    pinned = torch.empty(n + 16, dtype=torch.uint8).pin_memory()
+    pageable = np.empty(n + 16, np.uint8)
+    for off in (0, 1):
+        for dst in (dev, pinned):
+            view = dst[off:off + n]
+            view.fill_(7)
+            o = P.g.read(view)
+            torch.cuda.synchronize()
+            assert list(o) == list(P.o.o)
+            assert np.array_equal(view.cpu().numpy(), want), (dst.device, off)
+        view = pageable[off:off + n]
+        view[:] = 7
+        P.g.read(view)
+        torch.cuda.synchronize()
+        assert np.array_equal(view, want), ("pageable", off)
+    P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([0.5, -0.3, 0.2], -0.4))
+    P.close()
+
+
+def test_page_locked_host_inputs_are_read_in_place(vg):
+    w = make("paper", frames=2)
+    g = w.grid
+    P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos)
+    for f in w.frames:
+        d = torch.from_numpy(np.ascontiguousarray(f.depth)).pin_memory()
+        P.g.integrate_depth(d, f.T_wc, w.cam.scale)
+        P.o.integrate_depth(f.T_wc, f.depth, w.cam.scale)
+        P.check("pinned depth")
+    pts = np.random.default_rng(5).uniform([-2, -1, 0.2], [2, 1, 4], size=(3000, 3)).astype(np.float32)
+    T = w.frames[0].T_wc
+    P.g.integrate_points(torch.from_numpy(pts).pin_memory(), T)
+    P.o.integrate_points(T, pts)
+    P.check("pinned points")
+    P.close()
+
+
 def test_write_replaces_a_pending_shift(vg):
     rng = np.random.default_rng(15)
     P = _pair(vg, n=(40, 30, 16))
