@@ -320,21 +320,32 @@ VG_API int vg_batch_autotune(vg_batch *batch, const vg_frame *frames, int32_t n,
  * a pinned host pool for submitted frames and device staging for the frames
  * of the launches in flight.  A server thread forms batches from the queued
  * requests -- oldest first, at most one frame per camera per launch, so the
- * frames of one camera apply in submission order -- copies their depth to
- * the device on a copy stream while the previous launch computes, and runs
- * each batch as one fused launch (as vg_batch_step).  Requests that arrive
- * while launches are on the GPU join the next launch as soon as a launch
- * slot frees up.  Every entry point is thread-safe.
+ * frames of one camera apply in submission order -- and issues each batch
+ * in one of two ways.  A batch of at most plain_max frames runs each frame
+ * as the per-frame kernel chain of vg_integrate_depth on one of several
+ * streams (a camera always on the same one), K1 reading the frame in place
+ * from the pinned pool, so the frames of different cameras overlap on the
+ * device.  A larger batch has its depth copied to the device on a copy
+ * stream and runs as one fused launch (as vg_batch_step); fused launches
+ * are ordered after all earlier work of the server and before all later
+ * work.  Requests that arrive while launches are on the GPU join the next
+ * launch as soon as a launch slot frees up.  While launches are in flight
+ * the server thread polls their completion events (it keeps one CPU core
+ * busy meanwhile) and stamps each frame's completion as it is seen.  Every
+ * entry point is thread-safe.
  *
  *  memory_budget  bytes of device memory the server may hold: its staging
  *                 and tables plus the grids of the cameras it admits.
  *  max_batch      frames per launch (1 .. 4096).
  *  max_width, max_height
  *                 the largest depth frame a camera may submit.
- *  queue_depth    launches on the GPU at once (1 .. 8); 2 overlaps the next
- *                 launch's copies with the current launch.
+ *  queue_depth    launches on the GPU at once (1 .. 8); 2 or more overlap
+ *                 a launch with the next one's copies or kernels.
  *  pending_frames submitted frames the host pool holds (queued or in
  *                 flight) before vg_server_submit reports VG_EBUSY.
+ *  plain_max      the largest batch issued as per-frame kernel chains
+ *                 (0 .. 4096; 0 selects the default, 4); larger batches
+ *                 run as one fused launch.  Results do not depend on it.
  */
 typedef struct {
     int64_t memory_budget;
@@ -342,12 +353,13 @@ typedef struct {
     int32_t max_width, max_height;
     int32_t queue_depth;
     int32_t pending_frames;
+    int32_t plain_max;
 } vg_server_params;
 
 typedef struct {
     uint64_t submitted, completed, failed, batches;
     double mean_batch;        /* frames per launch */
-    double latency_p50_us;    /* submission to completion of the frame's launch */
+    double latency_p50_us;    /* submission to the moment the frame's device work is seen to end */
     double latency_p99_us;
     double latency_max_us;
     int64_t bytes_in_use;     /* device bytes held (staging, tables, grids) */

@@ -3,22 +3,32 @@
 //
 // Client threads submit frames (copied into a pinned host pool) into one
 // arrival-ordered queue.  The server thread repeatedly
-//   - finishes launches whose completion callback fired (status, latencies,
-//     freeing their pool slots and launch slot),
+//   - polls the completion events of the launches in flight, stamping each
+//     frame's completion time as soon as its work has ended, and retires a
+//     launch (status, latencies, pool slots, launch slot) once all of its
+//     frames have ended,
 //   - forms a batch when a launch slot is free: the oldest queued frames,
 //     at most one per camera, skipping cameras being read,
-//   - copies the batch's depth frames to device staging on the copy stream,
-//     makes the compute stream wait for the copies, and runs the batch as one
-//     fused launch (vg_batch_prepare + vg_batch_enqueue) on the compute stream,
-//     followed by a host callback that stamps the completion time.
-// With queue_depth >= 2 the copies of the next launch overlap the current
-// launch, and frames arriving meanwhile join the next launch.  Frames of one
-// camera apply in submission order: one per launch, launches in stream order.
+//   - issues the batch in one of two ways:
+//       small batches (at most plain_max frames): each frame runs the
+//       per-frame kernel chain (K1..K4, PDL-chained) on its camera's lane
+//       stream, K1 reading the frame in place from the pinned pool over the
+//       host link; frames of different cameras overlap on the device;
+//       larger batches: the depth frames are copied to device staging on
+//       the copy stream and the batch runs as one fused cooperative launch
+//       (vg_batch_prepare + vg_batch_enqueue) on the fused stream.
+// Frames of one camera apply in submission order: one per launch, launches
+// issued in order, a camera always on the same lane stream, and every fused
+// launch fenced both ways against the lanes (it waits for the lanes' work
+// issued before it, and lane work issued after it waits for it).  The fence
+// also means a cooperative launch never shares the device with this
+// server's other kernels, so its CTAs are all resident together.
 //
-// The mutex is never held across a CUDA call that could wait for the host
-// callback (the callback takes the mutex and makes no CUDA call), and the
-// server's streams are non-blocking so a synchronous copy elsewhere does not
-// wait for them.
+// While launches are in flight the server thread spins on their events
+// (cudaEventQuery) instead of sleeping, so a completion is seen within
+// microseconds; with nothing in flight it sleeps on the condition variable.
+// The mutex is never held across a CUDA call, and the server's streams are
+// non-blocking so a synchronous copy elsewhere does not wait for them.
 #include "vg.h"
 
 #include <cuda_runtime.h>
@@ -37,12 +47,20 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Lane streams for small batches; a camera always uses lane camera % kLanes.
+constexpr int kLanes = 8;
+// Default largest batch issued as per-frame chains (vg_server_params.plain_max == 0).
+constexpr int kDefaultPlainMax = 4;
+
 struct Request {
     uint64_t ticket;
     int32_t camera, slot, width, height, dtype, recentre;
     float scale;
     double T_wc[16], pos[3];
     Clock::time_point arrival;
+    Clock::time_point done_at;
+    int status;      // VG_OK, or the frame's error
+    bool ended;      // its device work has ended (or never started)
 };
 
 struct Camera {
@@ -54,23 +72,31 @@ struct Camera {
 };
 
 struct Launch {
-    vg_server *srv = nullptr;
     vg_batch *batch = nullptr;
-    uint8_t *staging = nullptr;   // max_batch frames of device staging
+    uint8_t *staging = nullptr;   // max_batch frames of device staging (fused launches)
     cudaEvent_t copied = nullptr;
+    cudaEvent_t done = nullptr;   // end of a fused launch
+    std::vector<cudaEvent_t> ev;  // end of each frame's chain (per-frame launches)
     std::vector<Request> reqs;
-    bool busy = false;
-    bool gpu_done = false;
-    Clock::time_point done_at;
+    bool busy = false;     // formed, not yet retired
+    bool issued = false;   // its device work has been enqueued
+    bool fused = false;
+    int remaining = 0;     // frames whose device work has not been seen to end
 };
 
 }  // namespace
 
 struct vg_server {
     vg_server_params p;
+    int plain_max = kDefaultPlainMax;
     int device = 0;
     size_t frame_bytes = 0;
     cudaStream_t compute = nullptr, copy = nullptr, admin = nullptr;
+    cudaStream_t lanes[kLanes] = {};
+    cudaEvent_t lane_tail[kLanes] = {};   // a lane's work before a fused launch
+    bool lane_dirty[kLanes] = {};         // work issued on the lane since the last fused fence
+    bool lane_behind[kLanes] = {};        // a fused launch was issued since the lane's last work
+    cudaEvent_t fused_tail = nullptr;     // end of the last fused launch
     uint8_t *pinned = nullptr;
     std::vector<int32_t> free_slots;
     std::vector<Camera> cams;
@@ -89,21 +115,6 @@ struct vg_server {
 
 namespace {
 
-void CUDART_CB on_launch_done(void *arg) {
-    Launch *L = static_cast<Launch *>(arg);
-    vg_server *S = L->srv;
-    std::lock_guard<std::mutex> g(S->mu);
-    L->gpu_done = true;
-    L->done_at = Clock::now();
-    S->cv.notify_all();
-}
-
-bool any_done(const vg_server *S) {
-    for (const Launch &L : S->launches)
-        if (L.busy && L.gpu_done) return true;
-    return false;
-}
-
 bool can_launch(const vg_server *S) {
     if (S->inflight >= S->p.queue_depth) return false;
     for (const Request &r : S->queue)
@@ -111,13 +122,13 @@ bool can_launch(const vg_server *S) {
     return false;
 }
 
-// Under the lock: retire a launch whose work ended with status st.
-void finish(vg_server *S, Launch &L, int st, Clock::time_point when) {
+// Under the lock: retire a launch all of whose frames have ended.
+void finish(vg_server *S, Launch &L) {
     for (const Request &r : L.reqs) {
-        S->status[r.ticket] = st == VG_OK ? 1 : 2;
-        if (st == VG_OK) {
+        S->status[r.ticket] = r.status == VG_OK ? 1 : 2;
+        if (r.status == VG_OK) {
             ++S->completed;
-            S->lat_us.push_back((float)std::chrono::duration<double, std::micro>(when - r.arrival).count());
+            S->lat_us.push_back((float)std::chrono::duration<double, std::micro>(r.done_at - r.arrival).count());
         } else {
             ++S->failed;
         }
@@ -128,14 +139,72 @@ void finish(vg_server *S, Launch &L, int st, Clock::time_point when) {
     S->batched_frames += L.reqs.size();
     L.reqs.clear();
     L.busy = false;
-    L.gpu_done = false;
+    L.issued = false;
     --S->inflight;
     S->cv.notify_all();
 }
 
-// Issues one formed batch; returns its status (VG_OK once enqueued).
-int issue(vg_server *S, Launch &L) {
+void end_frame(Request &r, int st, Clock::time_point when, int &remaining) {
+    if (r.ended) return;
+    r.ended = true;
+    r.status = st;
+    r.done_at = when;
+    --remaining;
+}
+
+// Server thread, no lock: notes which frames of an issued launch have ended.
+void poll(Launch &L) {
+    if (L.fused) {
+        const cudaError_t e = cudaEventQuery(L.done);
+        if (e == cudaErrorNotReady) return;
+        const Clock::time_point now = Clock::now();
+        const int st = e != cudaSuccess ? VG_ECUDA : vg_batch_status(L.batch);   // ended: no wait
+        for (Request &r : L.reqs) end_frame(r, st, now, L.remaining);
+        return;
+    }
+    for (size_t k = 0; k < L.reqs.size(); ++k) {
+        Request &r = L.reqs[k];
+        if (r.ended) continue;
+        const cudaError_t e = cudaEventQuery(L.ev[k]);
+        if (e == cudaErrorNotReady) continue;
+        end_frame(r, e == cudaSuccess ? VG_OK : VG_ECUDA, Clock::now(), L.remaining);
+    }
+}
+
+// Per-frame chains: each frame on its camera's lane, K1 reading the pinned
+// pool slot in place.  A frame whose work could not be enqueued ends now
+// with its error.
+void issue_lanes(vg_server *S, Launch &L) {
+    for (size_t k = 0; k < L.reqs.size(); ++k) {
+        Request &r = L.reqs[k];
+        const int lane = r.camera % kLanes;
+        cudaStream_t st = S->lanes[lane];
+        int rc = VG_OK;
+        if (S->lane_behind[lane]) {
+            if (cudaStreamWaitEvent(st, S->fused_tail, 0) != cudaSuccess) rc = VG_ECUDA;
+            else S->lane_behind[lane] = false;
+        }
+        S->lane_dirty[lane] = true;
+        vg_grid *grid = S->cams[r.camera].grid;
+        if (rc == VG_OK)
+            rc = vg_integrate_depth(grid, S->pinned + (size_t)r.slot * S->frame_bytes, VG_MEM_HOST, r.width,
+                                    r.height, r.dtype, r.scale, r.T_wc, st);
+        if (rc == VG_OK && r.recentre) rc = vg_shift(grid, r.pos, st);
+        if (rc == VG_OK && cudaEventRecord(L.ev[k], st) != cudaSuccess) rc = VG_ECUDA;
+        if (rc != VG_OK) end_frame(r, rc, Clock::now(), L.remaining);
+    }
+}
+
+// One fused launch, fenced against the lanes.  Returns VG_OK once enqueued.
+int issue_fused(vg_server *S, Launch &L) {
     const size_t n = L.reqs.size();
+    for (int i = 0; i < kLanes; ++i) {
+        if (!S->lane_dirty[i]) continue;
+        if (cudaEventRecord(S->lane_tail[i], S->lanes[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(S->compute, S->lane_tail[i], 0) != cudaSuccess)
+            return VG_ECUDA;
+        S->lane_dirty[i] = false;
+    }
     for (size_t k = 0; k < n; ++k) {
         const Request &r = L.reqs[k];
         const size_t bytes = (size_t)r.width * r.height * (r.dtype == VG_DEPTH_F32 ? 4 : 2);
@@ -162,23 +231,51 @@ int issue(vg_server *S, Launch &L) {
     }
     int rc = vg_batch_prepare(L.batch, fr.data(), (int32_t)n);
     if (rc == VG_OK) rc = vg_batch_enqueue(L.batch, S->compute);
-    if (rc == VG_OK && cudaLaunchHostFunc(S->compute, on_launch_done, &L) != cudaSuccess) rc = VG_ECUDA;
-    return rc;
+    if (rc != VG_OK) return rc;
+    if (cudaEventRecord(S->fused_tail, S->compute) != cudaSuccess) return VG_ECUDA;
+    for (int i = 0; i < kLanes; ++i) S->lane_behind[i] = true;
+    return cudaEventRecord(L.done, S->compute) == cudaSuccess ? VG_OK : VG_ECUDA;
+}
+
+void issue(vg_server *S, Launch &L) {
+    L.remaining = (int)L.reqs.size();
+    for (Request &r : L.reqs) r.ended = false;
+    L.fused = (int)L.reqs.size() > S->plain_max;
+    if (!L.fused) {
+        issue_lanes(S, L);
+        return;
+    }
+    const int rc = issue_fused(S, L);
+    if (rc != VG_OK) {
+        // nothing of this batch is waited for: end it here, once the
+        // copies that did start have ended
+        cudaStreamSynchronize(S->copy);
+        const Clock::time_point now = Clock::now();
+        for (Request &r : L.reqs) end_frame(r, rc, now, L.remaining);
+    }
 }
 
 void server_loop(vg_server *S) {
     cudaSetDevice(S->device);
     for (;;) {
+        bool in_flight = false;
         std::vector<Launch *> done;
+        for (Launch &L : S->launches) {
+            if (!L.busy || !L.issued) continue;
+            if (L.remaining > 0) poll(L);
+            if (L.remaining == 0) done.push_back(&L);
+            else in_flight = true;
+        }
         Launch *next = nullptr;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv.wait(lk, [&] {
-                return any_done(S) || can_launch(S) || (S->stop && S->queue.empty() && S->inflight == 0);
-            });
-            for (Launch &L : S->launches)
-                if (L.busy && L.gpu_done) done.push_back(&L);
-            if (done.empty() && S->stop && S->queue.empty() && S->inflight == 0) return;
+            for (Launch *L : done) finish(S, *L);
+            auto idle_exit = [&] { return S->stop && S->queue.empty() && S->inflight == 0; };
+            if (!in_flight && !can_launch(S)) {
+                if (idle_exit()) return;
+                S->cv.wait(lk, [&] { return can_launch(S) || idle_exit(); });
+                if (!can_launch(S)) return;   // idle_exit
+            }
             if (can_launch(S)) {
                 for (Launch &L : S->launches)
                     if (!L.busy) {
@@ -198,24 +295,14 @@ void server_loop(vg_server *S) {
                     it = S->queue.erase(it);
                 }
                 next->busy = true;
-                next->gpu_done = false;
                 ++S->inflight;
             }
         }
-        for (Launch *L : done) {
-            const int st = vg_batch_status(L->batch);   // the launch has ended; no wait
-            std::lock_guard<std::mutex> g(S->mu);
-            finish(S, *L, st, L->done_at);
-        }
         if (next) {
-            const int rc = issue(S, *next);
-            if (rc != VG_OK) {
-                // nothing of this batch reaches the callback: finish it here,
-                // once the copies that did start have ended
-                cudaStreamSynchronize(S->copy);
-                std::lock_guard<std::mutex> g(S->mu);
-                finish(S, *next, rc, Clock::now());
-            }
+            issue(S, *next);
+            next->issued = true;
+        } else if (in_flight) {
+            std::this_thread::yield();
         }
     }
 }
@@ -229,11 +316,12 @@ int vg_server_create(const vg_server_params *p, vg_server **out) {
     *out = nullptr;
     if (!p || p->max_batch < 1 || p->max_batch > 4096 || p->queue_depth < 1 || p->queue_depth > 8 ||
         p->max_width < 1 || p->max_height < 1 || (int64_t)p->max_width * p->max_height >= (int64_t(1) << 31) ||
-        p->pending_frames < p->max_batch || p->memory_budget <= 0)
+        p->pending_frames < p->max_batch || p->memory_budget <= 0 || p->plain_max < 0 || p->plain_max > 4096)
         return VG_EINVAL;
     vg_server *S = new (std::nothrow) vg_server();
     if (!S) return VG_ENOMEM;
     S->p = *p;
+    S->plain_max = p->plain_max ? p->plain_max : kDefaultPlainMax;
     S->frame_bytes = ((size_t)p->max_width * p->max_height * 4 + 255) & ~size_t(255);
     const size_t staging = S->frame_bytes * (size_t)p->max_batch;
     // staging and a generous bound on each launch's descriptor table
@@ -246,15 +334,26 @@ int vg_server_create(const vg_server_params *p, vg_server **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->admin, cudaStreamNonBlocking);
+    for (int i = 0; i < kLanes && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&S->lanes[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->lane_tail[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->fused_tail, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->pinned, S->frame_bytes * (size_t)p->pending_frames);
     int rc = e == cudaSuccess ? VG_OK : (e == cudaErrorMemoryAllocation ? VG_ENOMEM : VG_ECUDA);
     S->launches.resize((size_t)p->queue_depth);
     for (Launch &L : S->launches) {
         if (rc != VG_OK) break;
-        L.srv = S;
         rc = vg_batch_create(p->max_batch, &L.batch);
         if (rc == VG_OK && cudaMalloc((void **)&L.staging, staging) != cudaSuccess) rc = VG_ENOMEM;
         if (rc == VG_OK && cudaEventCreateWithFlags(&L.copied, cudaEventDisableTiming) != cudaSuccess) rc = VG_ECUDA;
+        if (rc == VG_OK && cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) rc = VG_ECUDA;
+        const int nev = std::min(S->plain_max, p->max_batch);
+        for (int k = 0; k < nev && rc == VG_OK; ++k) {
+            cudaEvent_t ev = nullptr;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) rc = VG_ECUDA;
+            else L.ev.push_back(ev);
+        }
     }
     if (rc != VG_OK) {
         vg_server_destroy(S);
@@ -284,11 +383,20 @@ void vg_server_destroy(vg_server *S) {
     cudaSetDevice(S->device);
     if (S->compute) cudaStreamSynchronize(S->compute);
     if (S->copy) cudaStreamSynchronize(S->copy);
+    for (int i = 0; i < kLanes; ++i)
+        if (S->lanes[i]) cudaStreamSynchronize(S->lanes[i]);
     for (Launch &L : S->launches) {
         vg_batch_destroy(L.batch);
         cudaFree(L.staging);
         if (L.copied) cudaEventDestroy(L.copied);
+        if (L.done) cudaEventDestroy(L.done);
+        for (cudaEvent_t ev : L.ev) cudaEventDestroy(ev);
     }
+    for (int i = 0; i < kLanes; ++i) {
+        if (S->lanes[i]) cudaStreamDestroy(S->lanes[i]);
+        if (S->lane_tail[i]) cudaEventDestroy(S->lane_tail[i]);
+    }
+    if (S->fused_tail) cudaEventDestroy(S->fused_tail);
     for (Camera &c : S->cams)
         if (c.grid) vg_destroy(c.grid);
     cudaFreeHost(S->pinned);

@@ -56,7 +56,8 @@ class vg_frame(C.Structure):
 
 class vg_server_params(C.Structure):
     _fields_ = [("memory_budget", C.c_int64), ("max_batch", C.c_int32), ("max_width", C.c_int32),
-                ("max_height", C.c_int32), ("queue_depth", C.c_int32), ("pending_frames", C.c_int32)]
+                ("max_height", C.c_int32), ("queue_depth", C.c_int32), ("pending_frames", C.c_int32),
+                ("plain_max", C.c_int32)]
 
 
 class vg_server_stats_t(C.Structure):
@@ -440,8 +441,9 @@ class Server:
     """Continuous-batching request loop over many cameras (vg_server_*)."""
 
     def __init__(self, memory_budget, max_batch=64, max_width=1280, max_height=720, queue_depth=2,
-                 pending_frames=None):
+                 pending_frames=None, plain_max=0):
         p = vg_server_params()
+        p.plain_max = int(plain_max)
         p.memory_budget = int(memory_budget)
         p.max_batch = int(max_batch)
         p.max_width = int(max_width)

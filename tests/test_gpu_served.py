@@ -61,7 +61,11 @@ def _submit_all(server, cam, w, tickets):
             threading.Event().wait(0.001)   # pool full: retry
 
 
-def test_same_result_alone_and_in_the_mix(vg):
+@pytest.mark.parametrize("plain_max", [1, 4096], ids=["fused-and-chains", "chains-only"])
+def test_same_result_alone_and_in_the_mix(vg, plain_max):
+    # plain_max 1: single-frame batches run as per-frame chains and larger
+    # ones as fused launches, so a camera's frames alternate between the two;
+    # 4096: every batch runs as per-frame chains on the lane streams
     target = make("robot", robot=30, frames=4)
     others = [make("robot", robot=40 + i, frames=3) for i in range(10)] + [make("hires", frames=2)]
 
@@ -75,7 +79,7 @@ def test_same_result_alone_and_in_the_mix(vg):
     s1.close()
 
     # in the mix: two client threads interleave all cameras' frames
-    s2 = vg.Server(8 << 30, max_batch=8, queue_depth=2, pending_frames=24)
+    s2 = vg.Server(8 << 30, max_batch=8, queue_depth=3, pending_frames=24, plain_max=plain_max)
     ws = [target] + others
     cams = [_add(s2, w) for w in ws]
     tickets = []
