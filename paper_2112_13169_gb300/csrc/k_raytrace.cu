@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_raytrace(const FrameArgs a, con
     // end of K2; the occupancy is read after the wait (every CTA has a
     // first group: the grid is no larger than the group count)
     Lane ln;
-    rt_setup<LPR>(a, S, blockIdx.x, ln);
+    rt_setup<LPR>(a, S, b, blockIdx.x, ln);
     pdl_wait();
     box_stage<units::LoadRO>(a, b, box_fr, box_tr, occ_box);
     unsigned visits = rt_walk<LPR, units::LoadRO, EXACT>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);

@@ -85,6 +85,7 @@ struct Ray {
     float fs[3];     // step as float
     int32_t s[3];    // step: -1, 0, +1
     int32_t dP[3];   // change of the plane bit index per step
+    int32_t dPb[3];  // change of the packed box index per step
     int32_t nx, ny, nz;
 };
 
@@ -332,6 +333,8 @@ __device__ __forceinline__ void frame_start(const FrameArgs &a, float S[3]) {
 struct Lane {
     Ray r;
     float c_hi;
+    float t_out;   // the ray's first crossing of a grid face on its way out
+    float t_box;   // the ray's first crossing of a camera-box face on its way out
     int32_t n0[3];
     int j;         // lane within the ray
     bool active;   // the lane has a ray
@@ -340,7 +343,8 @@ struct Lane {
 // Set-up of this thread's lane for group `group` of kThreads / LPR rays.
 // Reads no memory but its arguments.
 template <int LPR>
-__device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], int64_t group, Lane &ln) {
+__device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], const Box &bx, int64_t group,
+                                         Lane &ln) {
     const int lane = threadIdx.x & 31;
     const int j = lane & (LPR - 1);
     const int32_t width = 2 * a.hw + 1;
@@ -356,8 +360,16 @@ __device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], i
     r.nz = a.g.nz;
     float absD[3];
     {
-        const int32_t ra = ln.active ? (int32_t)(ray % width) - a.hw : 0;
-        const int32_t rb = ln.active ? (int32_t)(ray / width) - a.hh : 0;
+        int32_t ra = 0, rb = 0;
+        if (ln.active) {
+            if (nrays <= INT32_MAX) {   // 32-bit division where the ids allow it
+                ra = (int32_t)((uint32_t)ray % (uint32_t)width) - a.hw;
+                rb = (int32_t)((uint32_t)ray / (uint32_t)width) - a.hh;
+            } else {
+                ra = (int32_t)(ray % width) - a.hw;
+                rb = (int32_t)(ray / width) - a.hh;
+            }
+        }
         const float fa = (float)ra, fb = (float)rb, fvd = (float)a.vd;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -380,6 +392,31 @@ __device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], i
         r.dP[0] = r.s[0];
         r.dP[1] = r.s[1] * (int32_t)R;
         r.dP[2] = r.s[2] * (int32_t)R * a.g.ny;
+        r.dPb[0] = r.s[0];
+        r.dPb[1] = r.s[1] * (32 * kBoxW);
+        r.dPb[2] = r.s[2] * (32 * kBoxW * kBoxY);
+    }
+
+    // Exit times.  A crossing of axis k's face F happens at exactly
+    // cross_at((float)F, S_k, 1/D_k): the walker keeps F as an exact float
+    // and evaluates the same expression.  So a crossing with t below the
+    // first outward grid (box) face crossing keeps a voxel that is inside
+    // the grid (box) inside it.
+    {
+        const float glo[3] = {0.0f, 0.0f, 0.0f};
+        const float ghi[3] = {(float)a.g.nx, (float)a.g.ny, (float)a.g.nz};
+        const float blo[3] = {(float)(32 * bx.bw0), (float)bx.by0, (float)bx.bz0};
+        const float bhi[3] = {(float)(32 * (bx.bw0 + kBoxW)), (float)(bx.by0 + kBoxY), (float)(bx.bz0 + kBoxZ)};
+        float to = INFINITY, tb = INFINITY;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (r.s[k] != 0) {
+                to = fminf(to, cross_at(r.s[k] > 0 ? ghi[k] : glo[k], S[k], r.inv[k]));
+                tb = fminf(tb, cross_at(r.s[k] > 0 ? bhi[k] : blo[k], S[k], r.inv[k]));
+            }
+        }
+        ln.t_out = to;
+        ln.t_box = tb;
     }
 
     // this lane's slice of tau: the in-grid part of the segment is cut
@@ -410,6 +447,153 @@ __device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], i
     for (int k = 0; k < 3; ++k) ln.n0[k] = j > 0 ? crossings_before(r, k, absD[k], c_lo) : 0;
 }
 
+// One crossing of the fast walker (the caller has checked that tm, the
+// smallest of t0..t2, is below its limit): the axis with the smallest time
+// moves, the lowest axis on a tie, as in walker_next.  PB: also step the
+// packed box index.
+template <bool PB>
+__device__ __forceinline__ void fast_step(const Ray &r, float tm, float &t0, float &t1, float &t2, float &nb0,
+                                          float &nb1, float &nb2, uint32_t &P, uint32_t &Pb) {
+    const bool mx = (t0 == tm);
+    const bool my = !mx && (t1 == tm);
+    const bool mz = !mx && !my;
+    if (mx) {
+        nb0 = __fadd_rn(nb0, r.fs[0]);
+        t0 = cross_at(nb0, r.S[0], r.inv[0]);
+        P += (uint32_t)r.dP[0];
+        if (PB) Pb += (uint32_t)r.dPb[0];
+    }
+    if (my) {
+        nb1 = __fadd_rn(nb1, r.fs[1]);
+        t1 = cross_at(nb1, r.S[1], r.inv[1]);
+        P += (uint32_t)r.dP[1];
+        if (PB) Pb += (uint32_t)r.dPb[1];
+    }
+    if (mz) {
+        nb2 = __fadd_rn(nb2, r.fs[2]);
+        t2 = cross_at(nb2, r.S[2], r.inv[2]);
+        P += (uint32_t)r.dP[2];
+        if (PB) Pb += (uint32_t)r.dPb[2];
+    }
+}
+
+// Pass 1 of a lane: its in-grid visits in walk order into its buffer column
+// col[q * kThreads], box-packed while the walk is inside the camera box,
+// plane bit indices after that.  Returns false when the column overflows.
+//
+// Exact steps (walker_next, with in-grid tests) lead to the first in-grid
+// voxel.  From there the walk runs without tests while its next crossing is
+// before t_lim = min(c_hi, t_out): such a crossing keeps the voxel in the
+// grid, and one before t_box keeps a voxel that is in the box in it (the
+// box may be left early on a tie, which only means that later box voxels
+// are marked in the planes directly).  All lanes run the same loop, so a
+// warp stays converged.  If the walk leaves the grid within the slice,
+// exact steps finish it.
+__device__ __forceinline__ bool walk_record(const Ray &r, const Lane &ln, const int32_t n0[3], bool visit_start,
+                                            const Box &b, uint32_t R, uint32_t *col, int32_t &nvis) {
+    const float c_hi = ln.c_hi;
+    Walker w;
+    walker_init(w, r, n0, R);
+    bool more = visit_start ? true : walker_next(w, r, c_hi);
+    while (more && !in_grid(w, r)) {
+        if (gone(w, r)) return true;
+        more = walker_next(w, r, c_hi);
+    }
+    if (!more) return true;
+
+    float t0 = w.t0, t1 = w.t1, t2 = w.t2, nb0 = w.nb0, nb1 = w.nb1, nb2 = w.nb2;
+    uint32_t P = w.P;
+    const uint32_t dw = (uint32_t)((w.i0 >> 5) - b.bw0), dy = (uint32_t)(w.i1 - b.by0), dz = (uint32_t)(w.i2 - b.bz0);
+    bool inb = dw < kBoxW && dy < kBoxY && dz < kBoxZ;
+    uint32_t Pb = kBoxFlag | (((dz * kBoxY + dy) * kBoxW + dw) << 5) | ((uint32_t)w.i0 & 31u);
+    const float t_lim = fminf(c_hi, ln.t_out), t_b = ln.t_box;
+    float tm;
+    for (;;) {
+        if (nvis == kRtBuf) return false;
+        col[nvis * kThreads] = inb ? Pb : P;
+        ++nvis;
+        tm = fminf(t0, fminf(t1, t2));
+        if (!(tm < t_lim)) break;
+        inb = inb && tm < t_b;
+        fast_step<true>(r, tm, t0, t1, t2, nb0, nb1, nb2, P, Pb);
+    }
+    if (!(tm < c_hi)) return true;   // the next crossing is the next lane's
+
+    // the walk leaves the grid within this slice: exact steps from here
+    w.t0 = t0;
+    w.t1 = t1;
+    w.t2 = t2;
+    w.nb0 = nb0;
+    w.nb1 = nb1;
+    w.nb2 = nb2;
+    w.i0 = (int32_t)nb0 - (r.s[0] > 0 ? 1 : 0);
+    w.i1 = (int32_t)nb1 - (r.s[1] > 0 ? 1 : 0);
+    w.i2 = (int32_t)nb2 - (r.s[2] > 0 ? 1 : 0);
+    w.P = P;
+    more = walker_next(w, r, c_hi);
+    while (more) {
+        if (in_grid(w, r)) {
+            if (nvis == kRtBuf) return false;
+            col[nvis * kThreads] = w.P;
+            ++nvis;
+        } else if (gone(w, r)) {
+            break;
+        }
+        more = walker_next(w, r, c_hi);
+    }
+    return true;
+}
+
+// Index among the recorded visits of the first one the rays see occupied,
+// or -1; kChunk occupancy words in flight at a time (box visits read the
+// staged box).
+template <class L>
+__device__ __forceinline__ int32_t first_hit(const FrameArgs &a, const uint32_t *occ_box, const uint32_t *col,
+                                             int32_t nvis) {
+    for (int32_t q0 = 0; q0 < nvis; q0 += kChunk) {
+        uint32_t p[kChunk], v[kChunk];
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) p[c] = q0 + c < nvis ? col[(q0 + c) * kThreads] : 0u;
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) v[c] = q0 + c < nvis ? occ_word<L>(a, occ_box, p[c]) : 0u;
+        int32_t hit = -1;
+#pragma unroll
+        for (int c = kChunk - 1; c >= 0; --c)
+            if (q0 + c < nvis && ((v[c] >> (p[c] & 31u)) & 1u)) hit = q0 + c;
+        if (hit >= 0) return hit;
+    }
+    return -1;
+}
+
+// Marks the recorded visits: q < f_end free, the rest traced.  Runs of
+// visits of the same kind in the same 32-voxel word are OR-ed in a register
+// and written with one atomicOr, to the box arrays or the planes.  The key
+// of a run is the visit's word (p >> 5, which carries the box flag in bit
+// 26) with the kind in bit 31.
+__device__ __forceinline__ void mark_flush(const FrameArgs &a, uint32_t *box_fr, uint32_t *box_tr, uint32_t key,
+                                           uint32_t bits) {
+    if (!bits) return;
+    const bool traced = key >> 31;
+    if (key & (kBoxFlag >> 5)) atomicOr((traced ? box_tr : box_fr) + (key & (kBoxWords - 1)), bits);
+    else atomicOr((traced ? a.pl.tr : a.pl.fr) + (key & 0x03ffffffu), bits);
+}
+
+__device__ __forceinline__ void mark_visits(const FrameArgs &a, uint32_t *box_fr, uint32_t *box_tr,
+                                            const uint32_t *col, int32_t nvis, int32_t f_end) {
+    uint32_t key = 0xffffffffu, bits = 0;
+    for (int32_t q = 0; q < nvis; ++q) {
+        const uint32_t p = col[q * kThreads];
+        const uint32_t k = (p >> 5) | (q >= f_end ? 0x80000000u : 0u);
+        if (k != key) {
+            mark_flush(a, box_fr, box_tr, key, bits);
+            key = k;
+            bits = 0;
+        }
+        bits |= 1u << (p & 31u);
+    }
+    mark_flush(a, box_fr, box_tr, key, bits);
+}
+
 // The walk of one group of rays set up by rt_setup, by all threads of the
 // CTA; `buf` is this CTA's visit buffer (kRtBuf columns of kThreads words).
 // Returns this thread's in-grid visits.  Warp-synchronous (every lane of
@@ -434,38 +618,18 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
     unsigned visits = 0;
 
     // ---- pass 1: walk the slice once, keep its in-grid visits --------
+    // (box-packed visits first, then plane bit indices), then find the
+    // first occupied one
+    // (each phase starts with the warp reconverged, so that its lanes run
+    // the phase's loop together rather than in groups)
+    uint32_t *col = buf + threadIdx.x;
     int32_t nvis = 0, hit_at = -1;
     bool ovf = !buffered;
-    if (active && !ovf) {
-        Walker w;
-        walker_init(w, r, n0, R);
-        bool more = (j == 0 && !(a.lit & kLitSkipStart)) ? true : walker_next(w, r, c_hi);
-        while (more) {
-            if (in_grid(w, r)) {
-                if (nvis == kRtBuf) {
-                    ovf = true;
-                    break;
-                }
-                buf[nvis * kThreads + threadIdx.x] = pack_visit(w, b);
-                ++nvis;
-            } else if (gone(w, r)) {
-                break;
-            }
-            more = walker_next(w, r, c_hi);
-        }
-        // first occupied visit, kChunk occupancy words in flight at a time
-        for (int q0 = 0; !ovf && q0 < nvis && hit_at < 0; q0 += kChunk) {
-            uint32_t p[kChunk], v[kChunk];
-#pragma unroll
-            for (int c = 0; c < kChunk; ++c) p[c] = q0 + c < nvis ? buf[(q0 + c) * kThreads + threadIdx.x] : 0u;
-#pragma unroll
-            for (int c = 0; c < kChunk; ++c) v[c] = q0 + c < nvis ? occ_word<L>(a, occ_box, p[c]) : 0u;
-#pragma unroll
-            for (int c = kChunk - 1; c >= 0; --c)
-                if (q0 + c < nvis && ((v[c] >> (p[c] & 31u)) & 1u)) hit_at = q0 + c;
-        }
-    }
     const bool visit_start = j == 0 && !(a.lit & kLitSkipStart);
+    __syncwarp();
+    if (active && !ovf) ovf = !walk_record(r, ln, n0, visit_start, b, R, col, nvis);
+    __syncwarp();
+    if (active && !ovf) hit_at = first_hit<L>(a, occ_box, col, nvis);
     if (active && ovf) hit_at = walk_first_hit<L>(a, r, n0, visit_start, c_hi, b, occ_box, R);
 
     // ---- first lane of this ray with an occupied voxel ---------------
@@ -477,7 +641,12 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
     const int mode = j < F ? 0 : (j == F ? 1 : 2);
 
     // ---- pass 2: mark free / traced -----------------------------------
-    if (active && !ovf) {
+    if (!EXACT && active && !ovf) {
+        // free before the ray's first occupied voxel, traced from it on
+        // (its own traced mark is overridden by K4: it is in occ_inf)
+        mark_visits(a, box_fr, box_tr, col, nvis, mode == 0 ? nvis : (mode == 1 ? hit_at : 0));
+        visits += (unsigned)nvis;
+    } else if (active && !ovf) {
         Marks m;
         for (int q = 0; q < nvis; ++q) {
             if (mode == 1 && q == hit_at) continue;
@@ -500,7 +669,7 @@ __device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3
                                              int buffered, uint32_t *box_fr, uint32_t *box_tr,
                                              const uint32_t *occ_box, uint32_t *buf) {
     Lane ln;
-    rt_setup<LPR>(a, S, group, ln);
+    rt_setup<LPR>(a, S, b, group, ln);
     return rt_walk<LPR, L, EXACT>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
 }
 
