@@ -286,6 +286,40 @@ __device__ __forceinline__ uint8_t resolve(uint32_t oc, uint32_t f, uint32_t t, 
     return old;
 }
 
+// The same resolve for four voxels at once.  With the state codes
+// OCC = 2, FREE = 1, TRACED = 3, a word's codes are two bit masks, hi (bit
+// 1 of each code: occupied or traced) and lo (bit 0: free or traced), and
+// known marks the voxels that are not unknown.  expand4 spreads a nibble
+// into one 0/1 byte per bit (bit i times 2^(7i) lands on bit 8i; no other
+// product of the multiply lands on a byte's low bit).  merge4 then writes
+// the codes of voxels 4m..4m+3 over the four old bytes where known.
+__device__ __forceinline__ uint32_t expand4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
+
+template <bool RAYS_LAST = false>
+__device__ __forceinline__ void code_masks(uint32_t oc, uint32_t f, uint32_t t, uint32_t &hi, uint32_t &lo,
+                                           uint32_t &known) {
+    uint32_t occ, fr, tr;
+    if (!RAYS_LAST) {
+        occ = oc;
+        fr = f & ~oc;
+        tr = t & ~(f | oc);
+    } else {
+        fr = f;
+        tr = t & ~f;
+        occ = oc & ~(f | t);
+    }
+    hi = occ | tr;
+    lo = fr | tr;
+    known = occ | fr | tr;
+}
+
+__device__ __forceinline__ uint32_t merge4(uint32_t hi, uint32_t lo, uint32_t known, int m, uint32_t old) {
+    const int s = 4 * m;
+    const uint32_t kb = expand4((known >> s) & 15u);
+    const uint32_t code = (expand4((hi >> s) & 15u) << 1) | expand4((lo >> s) & 15u);
+    return (old & ~(kb * 0xffu)) | code;
+}
+
 template <bool ALIGN8, class L, bool RAYS_LAST = false>
 __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl, uint8_t *loc, int64_t w) {
     if (w >= g.words) return;
@@ -298,6 +332,8 @@ __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl,
     if (any == 0) return;
     const int nbits = min(32, g.nx - x0);
     uint8_t *Lp = loc + row * g.nx + x0;
+    uint32_t hi, lo, known;
+    code_masks<RAYS_LAST>(oc, f, t, hi, lo, known);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         if (8 * c >= nbits) break;
@@ -306,13 +342,9 @@ __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl,
         if (ALIGN8 && 8 * c + 8 <= nbits) {
             uint64_t *p = reinterpret_cast<uint64_t *>(Lp + 8 * c);
             const uint64_t old = (m == 0xffu) ? 0ull : *p;
-            uint64_t v = 0;
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const uint8_t ob = (uint8_t)(old >> (8 * b));
-                v |= (uint64_t)resolve<RAYS_LAST>(oc, f, t, 8 * c + b, ob) << (8 * b);
-            }
-            *p = v;
+            const uint32_t v0 = merge4(hi, lo, known, 2 * c, (uint32_t)old);
+            const uint32_t v1 = merge4(hi, lo, known, 2 * c + 1, (uint32_t)(old >> 32));
+            *p = ((uint64_t)v1 << 32) | v0;
         } else {
             for (int b = 8 * c; b < 8 * c + 8 && b < nbits; ++b)
                 if ((any >> b) & 1u) Lp[b] = resolve<RAYS_LAST>(oc, f, t, b, 0);
@@ -415,15 +447,14 @@ __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Plane
                 old[m] = v;
             }
         }
+        if ((oc | f | t) == 0) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            uint32_t v = 0;
+            for (int m = 0; m < 8; ++m) nv[m] = old[m];
+        } else {
+            uint32_t hi, lo, known;
+            code_masks<RAYS_LAST>(oc, f, t, hi, lo, known);
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const int k = 4 * m + b;
-                v |= (uint32_t)resolve<RAYS_LAST>(oc, f, t, k, (uint8_t)(old[m] >> (8 * b))) << (8 * b);
-            }
-            nv[m] = v;
+            for (int m = 0; m < 8; ++m) nv[m] = merge4(hi, lo, known, m, old[m]);
         }
         if (oc) {
             pl.occ_inf[w] = 0;
