@@ -350,8 +350,13 @@ __device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], c
     const int32_t width = 2 * a.hw + 1;
     const int64_t nrays = (int64_t)width * (2 * a.hh + 1);
     const uint32_t R = 32u * (uint32_t)a.g.wx;   // plane bits per row
-    const int rays_per_cta = kThreads / LPR;
-    const int64_t ray = group * rays_per_cta + threadIdx.x / LPR;
+    // Warp w of group g takes bundle w * G + g of 32 / LPR neighbouring rays
+    // (G groups in the frame), so the warps of one CTA sample rows spread
+    // over the whole image and CTAs get similar amounts of work (rays of
+    // rows near the image's top and bottom leave the grid early).
+    constexpr int kRaysPerWarp = 32 / LPR;
+    const int64_t G = (nrays + kThreads / LPR - 1) / (kThreads / LPR);
+    const int64_t ray = ((int64_t)(threadIdx.x >> 5) * G + group) * kRaysPerWarp + (lane / LPR);
     ln.active = ray < nrays;
     ln.j = j;
     Ray &r = ln.r;
@@ -555,7 +560,15 @@ __device__ __forceinline__ int32_t first_hit(const FrameArgs &a, const uint32_t 
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) p[c] = q0 + c < nvis ? col[(q0 + c) * kThreads] : 0u;
 #pragma unroll
-        for (int c = 0; c < kChunk; ++c) v[c] = q0 + c < nvis ? occ_word<L>(a, occ_box, p[c]) : 0u;
+        for (int c = 0; c < kChunk; ++c) {
+            // both sources without a branch: the box word (any index is in
+            // range) and, for a plane visit, the plane word
+            const bool isb = (p[c] & kBoxFlag) != 0;
+            const uint32_t vb = occ_box[(p[c] >> 5) & (kBoxWords - 1)];
+            uint32_t vg = 0;
+            if (!isb && q0 + c < nvis) vg = L::ld(a.occ_test + (p[c] >> 5));
+            v[c] = isb ? vb : vg;
+        }
         int32_t hit = -1;
 #pragma unroll
         for (int c = kChunk - 1; c >= 0; --c)
