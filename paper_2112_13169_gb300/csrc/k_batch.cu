@@ -4,7 +4,8 @@
 // with its own grid, resolution, voxel size and radius), the whole path:
 //   phase 1  K1 voxelize           units of 1024 pixels
 //   phase 2  K2 inflate            8 x 8 x 8-word tiles (radius 1..3)
-//   phase 3  K3 ray trace          groups of 256 / LPR rays
+//   phase 3  K3 ray trace          groups of at most 256 / LPR rays (a
+//                                  frame's rays spread over its units)
 //   phase 4  K4 merge              256 plane words
 // with a grid-wide barrier between phases.  A frame's re-centre (K5) is not
 // a phase: it is left pending on its grid and applied by that grid's next
@@ -76,9 +77,9 @@ __device__ bool grid_sync(BatchCtl *ctl, unsigned nblocks) {
 
 template <int LPR>
 __device__ __forceinline__ unsigned group_lpr(const BatchItem &it, const float S[3], const Box &b, int64_t grp,
-                                              uint32_t *box_fr, uint32_t *box_tr, const uint32_t *occ_box,
-                                              uint32_t *buf) {
-    return rt_group<LPR, units::LoadL2>(it.a, S, b, grp, it.buffered, box_fr, box_tr, occ_box, buf);
+                                              int64_t G, uint32_t *box_fr, uint32_t *box_tr,
+                                              const uint32_t *occ_box, uint32_t *buf) {
+    return rt_group<LPR, units::LoadL2>(it.a, S, b, grp, G, it.buffered, box_fr, box_tr, occ_box, buf);
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restrict__ items, BatchCtl *ctl) {
@@ -146,12 +147,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
                 b = box_of(S);
                 box_stage<units::LoadL2>(it.a, b, box_fr, box_tr, occ_box);
             }
+            // the frame's rays are spread over its G units of this phase
             const int64_t grp = u - it.off[2];
+            const int64_t G = (i + 1 < n ? items[i + 1].off[2] : ctl->total[2]) - it.off[2];
             unsigned visits;
             switch (it.lpr) {
-            case 8: visits = group_lpr<8>(it, S, b, grp, box_fr, box_tr, occ_box, dyn); break;
-            case 16: visits = group_lpr<16>(it, S, b, grp, box_fr, box_tr, occ_box, dyn); break;
-            default: visits = group_lpr<32>(it, S, b, grp, box_fr, box_tr, occ_box, dyn); break;
+            case 8: visits = group_lpr<8>(it, S, b, grp, G, box_fr, box_tr, occ_box, dyn); break;
+            case 16: visits = group_lpr<16>(it, S, b, grp, G, box_fr, box_tr, occ_box, dyn); break;
+            default: visits = group_lpr<32>(it, S, b, grp, G, box_fr, box_tr, occ_box, dyn); break;
             }
             if (it.a.stats) {
                 const unsigned total = __reduce_add_sync(kFull, visits);

@@ -16,18 +16,17 @@ __global__ void __launch_bounds__(kThreads, 5) k_raytrace(const FrameArgs a, con
     float S[3];
     frame_start(a, S);
     const Box b = box_of(S);
-    const int64_t nrays = (2 * (int64_t)a.hw + 1) * (2 * (int64_t)a.hh + 1);
-    const int64_t groups = (nrays + (kThreads / LPR) - 1) / (kThreads / LPR);
+    const int64_t groups = rt_groups<LPR>(a);
     // the first group's set-up needs only the pose, so it overlaps the
     // end of K2; the occupancy is read after the wait (every CTA has a
     // first group: the grid is no larger than the group count)
     Lane ln;
-    rt_setup<LPR>(a, S, b, blockIdx.x, ln);
+    rt_setup<LPR>(a, S, b, blockIdx.x, groups, ln);
     pdl_wait();
     box_stage<units::LoadRO>(a, b, box_fr, box_tr, occ_box);
     unsigned visits = rt_walk<LPR, units::LoadRO, EXACT>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
     for (int64_t grp = blockIdx.x + gridDim.x; grp < groups; grp += gridDim.x)
-        visits += rt_group<LPR, units::LoadRO, EXACT>(a, S, b, grp, buffered, box_fr, box_tr, occ_box, buf);
+        visits += rt_group<LPR, units::LoadRO, EXACT>(a, S, b, grp, groups, buffered, box_fr, box_tr, occ_box, buf);
     box_flush(a, b, box_fr, box_tr);
     if (a.stats) {
         const unsigned total = __reduce_add_sync(kFull, visits);

@@ -687,6 +687,21 @@ int vg_batch_tune(vg_batch *B, int32_t knob, int32_t value) {
     return VG_EINVAL;
 }
 
+namespace {
+
+// CTAs of the batch's cooperative launch: the occupancy limit, or the
+// ctas_per_sm knob when it is lower.  0 on error.
+int batch_blocks(const vg_batch *B) {
+    const int max_blocks = vg::batch_max_blocks(B->device);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device) != cudaSuccess) return 0;
+    int blocks = max_blocks;
+    if (B->ctas_per_sm > 0 && B->ctas_per_sm * sms < max_blocks) blocks = B->ctas_per_sm * sms;
+    return blocks;
+}
+
+}  // namespace
+
 int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
     if (!B || !frames || n < 1 || n > B->capacity) return VG_EINVAL;
     // every frame's grid is distinct and usable, before any state changes
@@ -771,6 +786,23 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
         }
         ++G->frames;
     }
+    // Phase 3 hands each CTA a contiguous run of units.  Unless the units
+    // fill whole rounds of the grid, some CTAs would take one more unit
+    // than others, so each frame's rays are spread over proportionally more
+    // (partly filled) units: G_i = ceil(groups_i * rounds * blocks / T).
+    {
+        const int64_t T = total[2];
+        const int64_t nb = batch_blocks(B);
+        if (nb < 1) return VG_ECUDA;
+        const int64_t slots = (T + nb - 1) / nb * nb;
+        int64_t off = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            const int64_t groups = (i + 1 < n ? items[i + 1].off[2] : T) - items[i].off[2];
+            items[i].off[2] = off;
+            off += (groups * slots + T - 1) / T;
+        }
+        total[2] = off;
+    }
     std::memset(ctl, 0, sizeof(*ctl));
     ctl->n = n;
     for (int p = 0; p < 4; ++p) ctl->total[p] = total[p];
@@ -784,13 +816,9 @@ int vg_batch_enqueue(vg_batch *B, void *stream) {
     DeviceGuard dg(B->device);
     if (!dg.ok) return VG_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    const int max_blocks = vg::batch_max_blocks(B->device);
-    int sms = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, B->device);
-    if (e != cudaSuccess) return status_of(e);
-    int blocks = max_blocks;
-    if (B->ctas_per_sm > 0 && B->ctas_per_sm * sms < max_blocks) blocks = B->ctas_per_sm * sms;
+    const int blocks = batch_blocks(B);
     if (blocks < 1) return VG_ECUDA;
+    cudaError_t e;
     // under stream capture the events must become record nodes of the graph,
     // so that every replay records them
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

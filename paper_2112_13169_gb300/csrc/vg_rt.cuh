@@ -340,22 +340,30 @@ struct Lane {
     bool active;   // the lane has a ray
 };
 
-// Set-up of this thread's lane for group `group` of kThreads / LPR rays.
-// Reads no memory but its arguments.
+// Number of groups of kThreads / LPR rays a frame's bundle needs.
+template <int LPR>
+__device__ __forceinline__ int64_t rt_groups(const FrameArgs &a) {
+    const int64_t nrays = (2 * (int64_t)a.hw + 1) * (2 * (int64_t)a.hh + 1);
+    return (nrays + kThreads / LPR - 1) / (kThreads / LPR);
+}
+
+// Set-up of this thread's lane for group `group` of the G >= rt_groups
+// groups the frame's rays are spread over.  Reads no memory but its
+// arguments.
 template <int LPR>
 __device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], const Box &bx, int64_t group,
-                                         Lane &ln) {
+                                         int64_t G, Lane &ln) {
     const int lane = threadIdx.x & 31;
     const int j = lane & (LPR - 1);
     const int32_t width = 2 * a.hw + 1;
     const int64_t nrays = (int64_t)width * (2 * a.hh + 1);
     const uint32_t R = 32u * (uint32_t)a.g.wx;   // plane bits per row
-    // Warp w of group g takes bundle w * G + g of 32 / LPR neighbouring rays
-    // (G groups in the frame), so the warps of one CTA sample rows spread
-    // over the whole image and CTAs get similar amounts of work (rays of
-    // rows near the image's top and bottom leave the grid early).
+    // Warp w of group g takes bundle w * G + g of 32 / LPR neighbouring rays,
+    // so the warps of one group sample rows spread over the whole image and
+    // groups get similar amounts of work (rays of rows near the image's top
+    // and bottom leave the grid early).  Bundles past the last ray are idle;
+    // with G above the frame's own group count they spread evenly too.
     constexpr int kRaysPerWarp = 32 / LPR;
-    const int64_t G = (nrays + kThreads / LPR - 1) / (kThreads / LPR);
     const int64_t ray = ((int64_t)(threadIdx.x >> 5) * G + group) * kRaysPerWarp + (lane / LPR);
     ln.active = ray < nrays;
     ln.j = j;
@@ -679,10 +687,10 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
 // One group of rays: rt_setup then rt_walk.
 template <int LPR, class L, bool EXACT = false>
 __device__ __forceinline__ unsigned rt_group(const FrameArgs &a, const float S[3], const Box &b, int64_t group,
-                                             int buffered, uint32_t *box_fr, uint32_t *box_tr,
+                                             int64_t G, int buffered, uint32_t *box_fr, uint32_t *box_tr,
                                              const uint32_t *occ_box, uint32_t *buf) {
     Lane ln;
-    rt_setup<LPR>(a, S, b, group, ln);
+    rt_setup<LPR>(a, S, b, group, G, ln);
     return rt_walk<LPR, L, EXACT>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
 }
 
