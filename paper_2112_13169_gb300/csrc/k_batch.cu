@@ -28,7 +28,10 @@ using namespace rt;
 
 constexpr int kDynWords = kRtBuf * kThreads;   // also covers an inflate tile of radius <= 3
 static_assert(units::inflate_smem_words<3, 8, 8, 8>(3) <= (size_t)kDynWords, "inflate tile fits");
-static_assert(units::kMergeShiftSmem <= 4 * kDynWords, "merge-with-shift staging fits");
+// a merge with a pending re-centre takes units of kMergeWords plane words:
+// twice the one-step kernel's, so that each CTA keeps more loads in flight
+constexpr int kMergeWords = kBatchMergeWords;
+static_assert(units::merge_shift_smem(kMergeWords) <= 4 * kDynWords, "merge-with-shift staging fits");
 
 __device__ __forceinline__ int find_item(const BatchItem *items, int n, int phase, int64_t u) {
     int lo = 0, hi = n - 1;
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
         const BatchItem &it = items[i];
         const int64_t w = (u - it.off[3]) * kThreads + threadIdx.x;
         if (it.loc_dst)
-            units::merge_shift_unit<units::LoadL2, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, it.loc_dst, it.dx, it.dy, it.dz,
+            units::merge_shift_unit<kMergeWords, units::LoadL2, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, it.loc_dst, it.dx, it.dy, it.dz,
                                                    u - it.off[3], reinterpret_cast<uint8_t *>(dyn));
         else if (it.align8) units::merge_word<true, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
         else units::merge_word<false, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);

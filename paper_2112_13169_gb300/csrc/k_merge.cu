@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256) k_merge_shift(const PlaneGeom g, Planes p
     __shared__ __align__(16) uint8_t sm[units::kMergeShiftSmem];
     pdl_trigger();
     pdl_wait();
-    units::merge_shift_unit<units::LoadRO, units::LoadPlain, RL>(g, pl, src, dst, dx, dy, dz, blockIdx.x, sm);
+    units::merge_shift_unit<256, units::LoadRO, units::LoadPlain, RL>(g, pl, src, dst, dx, dy, dz, blockIdx.x, sm);
 }
 
 // The literal loc_grid reading of Alg. 2: the occupied voxels of loc_grid,
@@ -72,7 +72,7 @@ cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s) {
-    const unsigned blocks = (unsigned)units::merge_shift_units(a.g);
+    const unsigned blocks = (unsigned)units::merge_shift_units<256>(a.g);
     if (blocks == 0) return cudaSuccess;
     if (a.lit & kLitRaysLast)
         return launch_pdl(k_merge_shift<true>, blocks, 256, 0, s, a.g, a.pl, (const uint8_t *)a.loc, dst, delta[0],

@@ -754,7 +754,7 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
         it.buffered = G->g.words < (int64_t(1) << 26) ? 1 : 0;
         const int64_t npix = (int64_t)f.width * f.height;
         const int64_t nrays = (2 * (int64_t)G->hw + 1) * (2 * (int64_t)G->hh + 1);
-        const int64_t units[5] = {
+        int64_t units[4] = {
             ((npix + 3) / 4 + 255) / 256,
             G->p.vox_inf > 0 ? (int64_t)it.tiles[0] * it.tiles[1] * it.tiles[2] : 0,
             (nrays + (256 / it.lpr) - 1) / (256 / it.lpr),
@@ -768,6 +768,7 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
             it.loc_dst = G->loc_alt;
             std::swap(G->loc, G->loc_alt);
             G->pend_on = false;
+            units[3] = (G->g.words + vg::kBatchMergeWords - 1) / vg::kBatchMergeWords;
         }
         if (f.recentre) {
             // left pending, for the grid's next merge (or read)

@@ -115,6 +115,10 @@ struct BatchItem {
     uint8_t *loc_dst;   // non-null: merge a.loc shifted by (dx, dy, dz) into loc_dst
 };
 
+// Plane words per phase-4 unit of a batch frame whose merge applies a
+// pending re-centre (other frames' units are 256 words, one per thread).
+constexpr int kBatchMergeWords = 512;
+
 // Control block of a batch launch, copied to the device with the items.
 struct BatchCtl {
     int32_t n;          // frames

@@ -359,76 +359,84 @@ __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl,
 }
 
 // K4 with a pending re-centre (Sec. IV-E followed by Alg. 3): unit u is the
-// 256 plane words u*256 .. u*256+255, and writes every voxel of the new grid
-// they cover, dst[i] = the merge of the measurement (whose planes are in the
-// new grid's frame) over src[i + delta], delta = dx + dy*Nx + dz*Nx*Ny, or
-// over unknown where that voxel of the old grid does not exist.  Clears the
-// plane words it reads, as merge_word does.
+// WPU plane words u*WPU .. u*WPU+WPU-1 (WPU a multiple of 256), and writes
+// every voxel of the new grid they cover, dst[i] = the merge of the
+// measurement (whose planes are in the new grid's frame) over src[i + delta],
+// delta = dx + dy*Nx + dz*Nx*Ny, or over unknown where that voxel of the old
+// grid does not exist.  Clears the plane words it reads, as merge_word does.
 //
-// Because the plane row pitch wx is a power of two, the 256 words are whole
-// rows (wx <= 256) or one part of a row (wx > 256), so the unit's voxels
-// are one contiguous range [b0, b1) of at most 8192 bytes of dst, and their
+// Because the plane row pitch wx is a power of two, the WPU words are whole
+// rows (wx <= WPU) or one part of a row (wx > WPU), so the unit's voxels are
+// one contiguous range [b0, b1) of at most 32*WPU bytes of dst, and their
 // sources one contiguous range of src.  The CTA stages the sources in shared
-// memory with aligned 16-byte loads, each thread resolves its 32 voxels,
-// and the results go back through shared memory to aligned 16-byte stores.
-// sm: 16-byte aligned, kMergeShiftSmem bytes.  Called by all threads of a
-// 256-thread CTA with the same u.  LS loads src (never written by the
+// memory with aligned 16-byte loads (all issued before the first wait, so a
+// larger unit keeps more bytes in flight), each thread resolves the 32
+// voxels of each of its WPU/256 words into a second shared buffer, and the
+// results go out as aligned 16-byte stores.
+// sm: 16-byte aligned, merge_shift_smem(WPU) bytes.  Called by all threads
+// of a 256-thread CTA with the same u.  LS loads src (never written by the
 // launch), LP the planes (cleared by the launch).
-constexpr int kMergeShiftSmem = 8192 + 64;
+__host__ __device__ constexpr int merge_shift_smem(int wpu) { return 2 * (32 * wpu + 32); }
+constexpr int kMergeShiftSmem = merge_shift_smem(256);
 
-template <class LS, class LP, bool RAYS_LAST = false>
+template <int WPU, class LS, class LP, bool RAYS_LAST = false>
 __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Planes &pl, const uint8_t *src,
                                                  uint8_t *dst, int32_t dx, int32_t dy, int32_t dz, int64_t u,
                                                  uint8_t *sm) {
+    static_assert(WPU % 256 == 0, "whole CTAs of words");
+    constexpr int kVox = 32 * WPU;
+    uint8_t *sm_src = sm;                 // staged sources, kVox + 16 bytes
+    uint8_t *sm_out = sm + kVox + 32;     // results, 16-byte aligned
     const int tid = threadIdx.x;
     const int64_t rows = (int64_t)g.ny * g.nz;
     int64_t b0, b1;
-    if (g.wx <= 256) {
-        const int64_t R = 256 / g.wx;
+    if (g.wx <= WPU) {
+        const int64_t R = WPU / g.wx;
         const int64_t r0 = u * R, r1 = min(r0 + R, rows);
         b0 = r0 * g.nx;
         b1 = r1 * g.nx;
     } else {
-        const int64_t per = g.wx / 256, row = u / per, xa = (u % per) * 8192;
+        const int64_t per = g.wx / WPU, row = u / per, xa = (u % per) * kVox;
         b0 = row * g.nx + min(xa, (int64_t)g.nx);
-        b1 = row * g.nx + min(xa + 8192, (int64_t)g.nx);
+        b1 = row * g.nx + min(xa + kVox, (int64_t)g.nx);
     }
     if (b0 >= b1) return;   // uniform over the CTA
     const int64_t off = (int64_t)dx + (int64_t)dy * g.nx + (int64_t)dz * g.nx * g.ny;
 
-    // stage src[s0, s1): bytes [A, A + 16*n16) land at sm[0 ..); the last
-    // chunk may reach 15 bytes past nvox, into the buffer's slack
+    // stage src[s0, s1): bytes [A, A + 16*n16) land at sm_src[0 ..); the
+    // last chunk may reach 15 bytes past nvox, into the buffer's slack
     const int64_t s0 = max(b0 + off, (int64_t)0), s1 = min(b1 + off, g.nvox);
     const int64_t A = s0 & ~int64_t(15);
     __syncthreads();   // sm may still be read by the CTA's previous unit
     if (s0 < s1) {
         const int n16 = (int)((s1 - A + 15) >> 4);
         for (int i = tid; i < n16; i += 256)
-            reinterpret_cast<uint4 *>(sm)[i] = LS::ld(reinterpret_cast<const uint4 *>(src + A) + i);
+            reinterpret_cast<uint4 *>(sm_src)[i] = LS::ld(reinterpret_cast<const uint4 *>(src + A) + i);
     }
     __syncthreads();
 
-    // this thread's plane word and its 32 voxels
-    const int64_t w = u * 256 + tid;
-    const int32_t x0 = (int32_t)(w % g.wx) * 32;
-    const bool mine = w < g.words && x0 < g.nx;
-    uint32_t nv[8];
-    int nbits = 0;
-    int64_t d = 0;
-    if (mine) {
+    // results at sm_out[q0 + (i - b0)], q0 = b0 mod 16, so that sm_out and
+    // dst agree on 16-byte alignment
+    const int q0 = (int)(b0 & 15);
+#pragma unroll 1
+    for (int k = 0; k < WPU / 256; ++k) {
+        // this thread's plane word and its 32 voxels
+        const int64_t w = u * WPU + k * 256 + tid;
+        const int32_t x0 = (int32_t)(w % g.wx) * 32;
+        if (!(w < g.words && x0 < g.nx)) continue;
         const int64_t row = w / g.wx;
         const int32_t y = (int32_t)(row % g.ny), z = (int32_t)(row / g.ny);
-        nbits = min(32, g.nx - x0);
-        d = row * g.nx + x0;
+        const int nbits = min(32, g.nx - x0);
+        const int64_t d = row * g.nx + x0;
         const uint32_t oc = LP::ld(pl.occ_inf + w), f = LP::ld(pl.fr + w), t = LP::ld(pl.tr + w);
         const int32_t sy = y + dy, sz = z + dz, sx0 = x0 + dx;
         const bool row_ok = (unsigned)sy < (unsigned)g.ny && (unsigned)sz < (unsigned)g.nz;
-        const int p = (int)(d + off - A);   // sm index of the first source voxel
+        const int p = (int)(d + off - A);   // sm_src index of the first source voxel
         uint32_t old[8];
         if (row_ok && sx0 >= 0 && sx0 + nbits <= g.nx) {
             // all present: aligned shared words and a funnel shift (bytes
             // past nbits are garbage and discarded)
-            const uint32_t *ws = reinterpret_cast<const uint32_t *>(sm + (p & ~3));
+            const uint32_t *ws = reinterpret_cast<const uint32_t *>(sm_src + (p & ~3));
             const int sh = (p & 3) * 8;
             uint32_t wv[9];
 #pragma unroll
@@ -441,12 +449,14 @@ __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Plane
                 uint32_t v = 0;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const int k = 4 * m + b;
-                    if (row_ok && k < nbits && (unsigned)(sx0 + k) < (unsigned)g.nx) v |= (uint32_t)sm[p + k] << (8 * b);
+                    const int kk = 4 * m + b;
+                    if (row_ok && kk < nbits && (unsigned)(sx0 + kk) < (unsigned)g.nx)
+                        v |= (uint32_t)sm_src[p + kk] << (8 * b);
                 }
                 old[m] = v;
             }
         }
+        uint32_t nv[8];
         if ((oc | f | t) == 0) {
 #pragma unroll
             for (int m = 0; m < 8; ++m) nv[m] = old[m];
@@ -455,30 +465,23 @@ __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Plane
             code_masks<RAYS_LAST>(oc, f, t, hi, lo, known);
 #pragma unroll
             for (int m = 0; m < 8; ++m) nv[m] = merge4(hi, lo, known, m, old[m]);
+            if (oc) {
+                pl.occ_inf[w] = 0;
+                pl.occ_raw[w] = 0;
+            }
+            if (f) pl.fr[w] = 0;
+            if (t) pl.tr[w] = 0;
         }
-        if (oc) {
-            pl.occ_inf[w] = 0;
-            pl.occ_raw[w] = 0;
-        }
-        if (f) pl.fr[w] = 0;
-        if (t) pl.tr[w] = 0;
-    }
-    __syncthreads();   // the staged sources are no longer read
-
-    // results at sm[q0 + (i - b0)], q0 = b0 mod 16, so that sm and dst
-    // agree on 16-byte alignment
-    const int q0 = (int)(b0 & 15);
-    if (mine) {
         const int q = q0 + (int)(d - b0);
         const bool words = (q & 3) == 0;
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             if (words && 4 * m + 4 <= nbits) {
-                *reinterpret_cast<uint32_t *>(sm + q + 4 * m) = nv[m];
+                *reinterpret_cast<uint32_t *>(sm_out + q + 4 * m) = nv[m];
             } else {
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
-                    if (4 * m + b < nbits) sm[q + 4 * m + b] = (uint8_t)(nv[m] >> (8 * b));
+                    if (4 * m + b < nbits) sm_out[q + 4 * m + b] = (uint8_t)(nv[m] >> (8 * b));
             }
         }
     }
@@ -486,23 +489,26 @@ __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Plane
     // [b0, h) and [t1, b1) bytewise, [h, t1) in aligned 16-byte chunks
     const int64_t h = min(b1, (b0 + 15) & ~int64_t(15));
     const int64_t t1 = max(h, b1 & ~int64_t(15));
-    const int64_t base = b0 - q0;   // dst address of sm[0]; a multiple of 16
+    const int64_t base = b0 - q0;   // dst address of sm_out[0]; a multiple of 16
     if (tid < 16) {
         const int64_t i = b0 + tid;
-        if (i < h) dst[i] = sm[i - base];
+        if (i < h) dst[i] = sm_out[i - base];
     } else if (tid < 32) {
         const int64_t i = t1 + (tid - 16);
-        if (i < b1) dst[i] = sm[i - base];
+        if (i < b1) dst[i] = sm_out[i - base];
     }
     const int n16o = (int)((t1 - h) >> 4);
     for (int i = tid; i < n16o; i += 256) {
         const int64_t at = h + 16 * (int64_t)i;
-        *reinterpret_cast<uint4 *>(dst + at) = *reinterpret_cast<const uint4 *>(sm + (at - base));
+        *reinterpret_cast<uint4 *>(dst + at) = *reinterpret_cast<const uint4 *>(sm_out + (at - base));
     }
 }
 
-// Units of merge_shift_unit for a grid: one per 256 plane words.
-__host__ __device__ __forceinline__ int64_t merge_shift_units(const PlaneGeom &g) { return (g.words + 255) / 256; }
+// Units of merge_shift_unit<WPU> for a grid.
+template <int WPU>
+__host__ __device__ __forceinline__ int64_t merge_shift_units(const PlaneGeom &g) {
+    return (g.words + WPU - 1) / WPU;
+}
 
 // ---------------------------------------------------------------------------
 // K5: shift loc_grid to re-centre it on the robot (Sec. IV-E).
