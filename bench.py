@@ -67,37 +67,41 @@ def parse():
 # distributed plumbing (independent robots per rank)
 # ---------------------------------------------------------------------------
 class Dist:
-    def __init__(self, gpus):
+    """Ranks of a torchrun launch (RANK / LOCAL_RANK / WORLD_SIZE / MASTER_*
+    from the environment).  Only the barrier and the max / sum of the
+    timings cross ranks; the data path has no collective.  backend: "nccl"
+    on GPUs, "gloo" for the host-only tests of this plumbing."""
+
+    def __init__(self, gpus, backend="nccl"):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         if gpus != self.world:
             raise SystemExit("--gpus %d but WORLD_SIZE %d: launch N>1 with torchrun" % (gpus, self.world))
         self.pg = None
+        self.device = "cuda" if backend == "nccl" else "cpu"
         if self.world > 1:
             import torch.distributed as dist
-            dist.init_process_group("nccl")
+            dist.init_process_group(backend)
             self.pg = dist
 
     def barrier(self):
         if self.pg:
             self.pg.barrier()
 
-    def max(self, v):
+    def _reduce(self, v, op):
         if not self.pg:
             return v
         import torch
-        t = torch.tensor([float(v)], device="cuda")
-        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        t = torch.tensor([float(v)], dtype=torch.float64, device=self.device)
+        self.pg.all_reduce(t, op=op)
         return float(t.item())
 
+    def max(self, v):
+        return self._reduce(v, self.pg.ReduceOp.MAX if self.pg else None)
+
     def sum(self, v):
-        if not self.pg:
-            return v
-        import torch
-        t = torch.tensor([float(v)], device="cuda")
-        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
-        return float(t.item())
+        return self._reduce(v, self.pg.ReduceOp.SUM if self.pg else None)
 
     def close(self):
         if self.pg:
@@ -565,6 +569,12 @@ def measure_served(vg, args, rank):
     return out
 
 
+def rank_seed(rank):
+    """Seed of the robot sequence rank `rank` runs (None: the workload's own
+    seed).  Every rank runs an independent robot: weak scaling."""
+    return None if rank == 0 else 2000 + 17 * rank
+
+
 def run_ours(args):
     import torch
     from paper_2112_13169_gb300 import build as vgbuild
@@ -574,8 +584,7 @@ def run_ours(args):
     from paper_2112_13169_gb300 import vg
     from synth import make
 
-    seed = None if dist.rank == 0 else 2000 + 17 * dist.rank
-    w = make(args.workload, frames=args.frames, seed=seed)
+    w = make(args.workload, frames=args.frames, seed=rank_seed(dist.rank))
     g = w.grid
     F = len(w.frames)
     stream = torch.cuda.current_stream()
