@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--serve-cameras", type=int, default=256, help="cameras of the served form (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="seconds of Poisson arrivals")
     ap.add_argument("--serve-rate", type=float, default=30.0, help="frames per second per camera")
+    ap.add_argument("--serve-rate-high", type=float, default=60.0,
+                    help="frames per second per camera of a second, heavier served run (0: skip)")
+    ap.add_argument("--serve-seconds-high", type=float, default=2.0, help="seconds of arrivals of that run")
     ap.add_argument("--serve-queue-depth", type=int, default=4, help="launches the server keeps in flight")
     ap.add_argument("--serve-plain-max", type=int, default=0,
                     help="largest served batch run as per-frame kernel chains (0: library default)")
@@ -688,6 +691,11 @@ def run_ours(args):
         forms["multi_robot"] = measure_batched(vg, args, dist.rank, stream)
     if args.serve_cameras > 0:
         forms["served"] = measure_served(vg, args, dist.rank)
+        if args.serve_rate_high > 0:
+            # twice the stated load: the one-frame-at-a-time queue falls behind
+            hi = argparse.Namespace(**vars(args))
+            hi.serve_rate, hi.serve_seconds = args.serve_rate_high, args.serve_seconds_high
+            forms["served_high_load"] = measure_served(vg, hi, dist.rank)
     t_forms_end = time.time()
 
     if clocks:
