@@ -154,37 +154,72 @@ def make_params(n, vox_size, fov_x_deg, fov_y_deg, depth, vox_inf, flags=0):
     return p
 
 
+# torch is optional (numpy buffers work without it); looked up once
+_TORCH = None
+_TORCH_DTYPES = None
+_CUDA = None
+
+
+def _torch():
+    global _TORCH, _TORCH_DTYPES
+    if _TORCH is None:
+        try:
+            import torch
+        except ImportError:
+            _TORCH = False
+            return None
+        _TORCH = torch
+        _TORCH_DTYPES = {torch.float32: "float32", torch.uint16: "uint16", torch.uint8: "uint8",
+                         torch.float64: "float64", torch.int32: "int32", torch.int16: "int16"}
+    return _TORCH or None
+
+
 def _stream(stream):
+    """The cudaStream_t (an integer) to pass for `stream`."""
+    global _CUDA
     if stream is None:
-        import torch
-        if torch.cuda.is_available():
-            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
-        return C.c_void_p(0)
+        t = _torch()
+        if _CUDA is None:
+            _CUDA = bool(t is not None and t.cuda.is_available())
+        return t.cuda.current_stream().cuda_stream if _CUDA else 0
     if isinstance(stream, int):
-        return C.c_void_p(stream)
-    return C.c_void_p(stream.cuda_stream)
+        return stream
+    return stream.cuda_stream
 
 
 def _buffer(x):
     """(pointer, mem kind, nbytes, dtype string) of a tensor or array."""
-    try:
-        import torch
-        if isinstance(x, torch.Tensor):
-            if not x.is_contiguous():
-                raise ValueError("buffer must be contiguous")
-            mem = VG_MEM_DEVICE if x.is_cuda else VG_MEM_HOST
-            return x.data_ptr(), mem, x.numel() * x.element_size(), str(x.dtype).replace("torch.", "")
-    except ImportError:
-        pass
+    t = _torch()
+    if t is not None and isinstance(x, t.Tensor):
+        if not x.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        dt = _TORCH_DTYPES.get(x.dtype) or str(x.dtype).replace("torch.", "")
+        return x.data_ptr(), (VG_MEM_DEVICE if x.is_cuda else VG_MEM_HOST), x.numel() * x.element_size(), dt
     a = x
     if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
         raise ValueError("buffer must be a contiguous numpy array or torch tensor")
-    return a.ctypes.data, VG_MEM_HOST, a.nbytes, str(a.dtype)
+    return a.ctypes.data, VG_MEM_HOST, a.nbytes, a.dtype.name
 
 
 def _f64(v, n):
-    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(n))
-    return a, a.ctypes.data_as(C.c_void_p)
+    """(array, pointer) of v as n contiguous float64 values; the array must
+    outlive the call that uses the pointer."""
+    if type(v) is np.ndarray and v.dtype is _F64 and v.size == n and v.flags.c_contiguous:
+        a = v
+    else:
+        a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(n))
+    return a, a.__array_interface__["data"][0]
+
+
+_F64 = np.dtype(np.float64)
+_DEPTH_DTYPES = {"float32": VG_DEPTH_F32, "uint16": VG_DEPTH_U16}
+
+
+def _depth_dtype(dt):
+    d = _DEPTH_DTYPES.get(dt)
+    if d is None:
+        raise ValueError("depth must be float32 or uint16, got " + dt)
+    return d
 
 
 def vg_grid_bytes(params):
@@ -211,16 +246,11 @@ def vg_destroy(h):
 
 def vg_integrate_depth(h, depth, T_wc, depth_scale=1.0, stream=None):
     ptr, mem, nbytes, dt = _buffer(depth)
-    if dt == "float32":
-        dtype = VG_DEPTH_F32
-    elif dt == "uint16":
-        dtype = VG_DEPTH_U16
-    else:
-        raise ValueError("depth must be float32 or uint16, got " + dt)
+    dtype = _depth_dtype(dt)
     H, W = depth.shape
     T, tp = _f64(T_wc, 16)
-    _check(load().vg_integrate_depth(h, C.c_void_p(ptr), mem, int(W), int(H), dtype, float(depth_scale),
-                                     tp, _stream(stream)), "vg_integrate_depth")
+    _check((_LIB or load()).vg_integrate_depth(h, ptr, mem, W, H, dtype, depth_scale, tp, _stream(stream)),
+           "vg_integrate_depth")
 
 
 def vg_integrate_depth_noalloc(params, origin, loc, depth, T_wc, depth_scale=1.0, stream=None):
@@ -236,18 +266,12 @@ def vg_integrate_depth_noalloc(params, origin, loc, depth, T_wc, depth_scale=1.0
     n = params.grid_size
     if ldt != "uint8" or lbytes != n[0] * n[1] * n[2]:
         raise ValueError("loc must hold Nx*Ny*Nz uint8 voxels")
-    if dt == "float32":
-        dtype = VG_DEPTH_F32
-    elif dt == "uint16":
-        dtype = VG_DEPTH_U16
-    else:
-        raise ValueError("depth must be float32 or uint16, got " + dt)
+    dtype = _depth_dtype(dt)
     H, W = depth.shape
     o = np.ascontiguousarray(np.asarray(origin, np.int32).reshape(3))
     T, tp = _f64(T_wc, 16)
-    _check(load().vg_integrate_depth_noalloc(C.byref(params), o.ctypes.data_as(C.c_void_p), C.c_void_p(lptr),
-                                             C.c_void_p(dptr), int(W), int(H), dtype, float(depth_scale), tp,
-                                             _stream(stream)), "vg_integrate_depth_noalloc")
+    _check(load().vg_integrate_depth_noalloc(C.byref(params), o.ctypes.data, lptr, dptr, int(W), int(H), dtype,
+                                             float(depth_scale), tp, _stream(stream)), "vg_integrate_depth_noalloc")
 
 
 def vg_integrate_points(h, xyz, T_wc, stream=None):
@@ -255,34 +279,31 @@ def vg_integrate_points(h, xyz, T_wc, stream=None):
     if dt != "float32":
         raise ValueError("points must be float32 xyz triples")
     T, tp = _f64(T_wc, 16)
-    _check(load().vg_integrate_points(h, C.c_void_p(ptr), mem, nbytes // 12, tp, _stream(stream)),
-           "vg_integrate_points")
+    _check(load().vg_integrate_points(h, ptr, mem, nbytes // 12, tp, _stream(stream)), "vg_integrate_points")
 
 
 def vg_shift(h, robot_pos_w, stream=None):
     pos, pp = _f64(robot_pos_w, 3)
-    _check(load().vg_shift(h, pp, _stream(stream)), "vg_shift")
+    _check((_LIB or load()).vg_shift(h, pp, _stream(stream)), "vg_shift")
 
 
 def vg_read(h, dst, stream=None):
     """Enqueue a copy of loc_grid into dst; returns the origin (int32[3])."""
     ptr, mem, nbytes, _ = _buffer(dst)
     o = np.zeros(3, np.int32)
-    _check(load().vg_read(h, C.c_void_p(ptr), mem, nbytes, o.ctypes.data_as(C.c_void_p), _stream(stream)),
-           "vg_read")
+    _check((_LIB or load()).vg_read(h, ptr, mem, nbytes, o.ctypes.data, _stream(stream)), "vg_read")
     return o
 
 
 def vg_write(h, src, origin, stream=None):
     ptr, mem, nbytes, _ = _buffer(src)
     o = np.ascontiguousarray(np.asarray(origin, np.int32).reshape(3))
-    _check(load().vg_write(h, C.c_void_p(ptr), mem, nbytes, o.ctypes.data_as(C.c_void_p), _stream(stream)),
-           "vg_write")
+    _check(load().vg_write(h, ptr, mem, nbytes, o.ctypes.data, _stream(stream)), "vg_write")
 
 
 def vg_get_origin(h):
     o = np.zeros(3, np.int32)
-    _check(load().vg_get_origin(h, o.ctypes.data_as(C.c_void_p)), "vg_get_origin")
+    _check(load().vg_get_origin(h, o.ctypes.data), "vg_get_origin")
     return o
 
 
@@ -383,13 +404,12 @@ def make_frames(frames):
         fr.width, fr.height = int(W), int(H)
         fr.dtype = VG_DEPTH_F32 if dt == "float32" else VG_DEPTH_U16
         fr.depth_scale = float(scale)
-        T = np.asarray(T_wc, np.float64).reshape(16)
-        for k in range(16):
-            fr.T_wc[k] = float(T[k])
+        T, tp = _f64(T_wc, 16)
+        C.memmove(fr.T_wc, tp, 128)
         if pos is not None:
             fr.recentre = 1
-            for k in range(3):
-                fr.robot_pos_w[k] = float(pos[k])
+            P, pp = _f64(pos, 3)
+            C.memmove(fr.robot_pos_w, pp, 24)
     return arr
 
 
@@ -469,15 +489,13 @@ class Server:
         ptr, mem, nbytes, dt = _buffer(depth)
         if mem != VG_MEM_HOST:
             raise ValueError("served frames come from host memory")
-        dtype = VG_DEPTH_F32 if dt == "float32" else VG_DEPTH_U16 if dt == "uint16" else None
-        if dtype is None:
-            raise ValueError("depth must be float32 or uint16, got " + dt)
+        dtype = _depth_dtype(dt)
         H, W = depth.shape
         T, tp = _f64(T_wc, 16)
-        pos, pp = _f64(robot_pos_w if robot_pos_w is not None else (0, 0, 0), 3)
+        pos, pp = _f64(robot_pos_w if robot_pos_w is not None else (0.0, 0.0, 0.0), 3)
         t = C.c_uint64()
-        rc = load().vg_server_submit(self.h, int(camera), C.c_void_p(ptr), int(W), int(H), dtype,
-                                     float(depth_scale), tp, 1 if robot_pos_w is not None else 0, pp, C.byref(t))
+        rc = load().vg_server_submit(self.h, int(camera), ptr, int(W), int(H), dtype, float(depth_scale), tp,
+                                     1 if robot_pos_w is not None else 0, pp, C.byref(t))
         if rc == VG_EBUSY:
             return None
         _check(rc, "vg_server_submit")
@@ -489,8 +507,7 @@ class Server:
     def read(self, camera, dst):
         ptr, mem, nbytes, _ = _buffer(dst)
         o = np.zeros(3, np.int32)
-        _check(load().vg_server_read(self.h, int(camera), C.c_void_p(ptr), mem, nbytes,
-                                     o.ctypes.data_as(C.c_void_p)), "vg_server_read")
+        _check(load().vg_server_read(self.h, int(camera), ptr, mem, nbytes, o.ctypes.data), "vg_server_read")
         return o
 
     def stats(self, reset=False):
