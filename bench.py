@@ -238,7 +238,9 @@ def workload_config(w, args):
 # our arm
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(kind, w, geom):
-    """Bytes one launch of a kernel must move at minimum."""
+    """Bytes one launch of a kernel must move at minimum: its inputs read
+    once and its outputs written once (bit planes of `words` 32-bit words,
+    the 1-byte-per-voxel loc grid, the depth image)."""
     nvox = w.nvox
     words = geom["words"]
     px = w.cam.W * w.cam.H * (2 if w.cam.dtype == "u16" else 4)
