@@ -151,3 +151,28 @@ def test_null_handles_are_rejected(vg):
     assert L.vg_tune(None, 0, 8) == vg.VG_EINVAL
     L.vg_destroy(None)
     assert vg.strerror(vg.VG_EINVAL) == "invalid argument"
+
+
+@pytest.mark.parametrize("field,value", [("max_batch", 0), ("queue_depth", 0), ("queue_depth", 9),
+                                         ("pending_frames", 1), ("memory_budget", 0), ("plain_max", -1),
+                                         ("plain_max", 5000), ("max_width", 0)])
+def test_server_rejects_bad_params_before_any_device_work(vg, field, value):
+    p = vg.vg_server_params()
+    p.memory_budget, p.max_batch, p.max_width, p.max_height = 1 << 30, 8, 640, 480
+    p.queue_depth, p.pending_frames, p.plain_max = 2, 16, 0
+    setattr(p, field, value)
+    h = C.c_void_p()
+    assert vg.load().vg_server_create(C.byref(p), C.byref(h)) == vg.VG_EINVAL
+    assert not h.value
+
+
+def test_batch_and_server_null_handles(vg):
+    L = vg.load()
+    assert L.vg_batch_prepare(None, None, 1) == vg.VG_EINVAL
+    assert L.vg_batch_enqueue(None, None) == vg.VG_EINVAL
+    assert L.vg_batch_status(None) == vg.VG_EINVAL
+    assert L.vg_server_wait(None, 0, 0) == vg.VG_EINVAL
+    st = vg.vg_server_stats_t()
+    assert L.vg_server_stats(None, C.byref(st), 0) == vg.VG_EINVAL
+    L.vg_batch_destroy(None)
+    L.vg_server_destroy(None)
