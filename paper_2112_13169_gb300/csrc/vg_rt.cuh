@@ -2,7 +2,6 @@
 // group of rays, shared by the one-kernel-per-step launch (k_raytrace.cu)
 // and the fused persistent launch (k_batch.cu).
 //
-//
 // Ray bundle: one ray per far-plane voxel (a, b, vox_depth) of the camera,
 // a in [-hw, hw], b in [-hh, hh]; ray id = (b + hh) * (2hw + 1) + (a + hw).
 // In voxel units the ray is the segment S + tau * D, tau in [0, 1], with
@@ -29,29 +28,42 @@
 //
 // Parallel walk.  LPR lanes of a warp share one ray.  Lane j owns the face
 // crossings with tau in [c_j, c_{j+1}), c_0 = -inf, c_LPR = 1, and the
-// other cuts split the part of the segment inside the grid evenly.  Because each axis's crossing times are non-decreasing in m,
-// the serial walk performs exactly the crossings with t < c_j before any
-// other, so lane j starts from voxel floor(S) + step * n(c_j), with
-// n_k(c) = #{m : t_k(m) < c} found by an estimate and an exact fix-up on
-// the same float expression, and then merges the three axes exactly as the
-// serial walk does.  The lanes' visit lists concatenate to the serial list.
+// other cuts split the part of the segment inside the grid evenly.  Because
+// each axis's crossing times are non-decreasing in m, the serial walk
+// performs exactly the crossings with t < c_j before any other, so lane j
+// starts from voxel floor(S) + step * n(c_j), with n_k(c) = #{m : t_k(m) < c}
+// found by an estimate and an exact fix-up on the same float expression,
+// and then merges the three axes exactly as the serial walk does.  The
+// lanes' visit lists concatenate to the serial list.
+//
+// Fast walk.  A crossing of axis k's face F happens at exactly the float
+// time ((float)F - S_k) * (1/D_k), because the walker keeps F as an exact
+// float and evaluates that expression.  So while the next crossing is
+// earlier than the ray's first outward grid-face crossing t_out (computed
+// once with the same expression), a voxel inside the grid stays inside, and
+// likewise for the camera box and t_box: the walk needs no per-step bounds
+// or box tests.  Exact steps (with tests) lead to a lane's first in-grid
+// voxel and finish a slice in which the ray leaves the grid.
 //
 // Pass 1: each lane walks its slice once and keeps its in-grid visits in
 // its own shared-memory column (kRtBuf entries), then finds the first
 // occupied one, kChunk occupancy words in flight at a time.  A ballot over
 // the ray's lanes gives the first lane F that met one.
-// Pass 2: each lane replays its visits and marks: lanes before F all free;
-// lane F free before its occupied voxel and traced after it; lanes after F
-// traced.  Marks after the first occupied voxel are written without
-// re-reading the occupancy: a traced mark on an occupied voxel is
+// Pass 2: each lane replays its visits and marks: free before the ray's
+// first occupied voxel, traced from it on (lanes before F all free, lanes
+// after F all traced).  Traced marks are written without re-reading the
+// occupancy: a traced mark on an occupied voxel, the first one included, is
 // overridden by K4.  Marks that fall in the same 32-voxel word are OR-ed in
 // a register and flushed with one atomicOr; near the camera, where all rays
 // overlap, they go to a per-CTA shared-memory box first (see kBoxW).
 // A lane whose slice holds more than kRtBuf in-grid visits, or a grid whose
 // planes are too large for a packed visit, walks twice instead.
 //
-// The CTAs are persistent: each loops over groups of kThreads / LPR rays,
-// so the box is staged and flushed once per CTA.
+// Work mapping: warp w of group g takes a bundle of 32 / LPR neighbouring
+// rays, bundle w * G + g of the frame's G groups, so every group samples
+// rows across the whole image (rows near the top and bottom leave the grid
+// early).  The CTAs are persistent: each loops over groups, so the box is
+// staged and flushed once per CTA.
 #pragma once
 
 #include "vg_units.cuh"
