@@ -54,6 +54,7 @@ constexpr int kDefaultPlainMax = 4;
 
 struct Request {
     uint64_t ticket;
+    vg_grid *grid;   // the camera's grid, captured under the lock when the batch is formed
     int32_t camera, slot, width, height, dtype, recentre;
     float scale;
     double T_wc[16], pos[3];
@@ -185,7 +186,7 @@ void issue_lanes(vg_server *S, Launch &L) {
             else S->lane_behind[lane] = false;
         }
         S->lane_dirty[lane] = true;
-        vg_grid *grid = S->cams[r.camera].grid;
+        vg_grid *grid = r.grid;
         if (rc == VG_OK)
             rc = vg_integrate_depth(grid, S->pinned + (size_t)r.slot * S->frame_bytes, VG_MEM_HOST, r.width,
                                     r.height, r.dtype, r.scale, r.T_wc, st);
@@ -219,7 +220,7 @@ int issue_fused(vg_server *S, Launch &L) {
         const Request &r = L.reqs[k];
         vg_frame &f = fr[k];
         std::memset(&f, 0, sizeof(f));
-        f.grid = S->cams[r.camera].grid;
+        f.grid = r.grid;
         f.depth = L.staging + k * S->frame_bytes;
         f.width = r.width;
         f.height = r.height;
@@ -292,6 +293,10 @@ void server_loop(vg_server *S) {
                     }
                     used[it->camera] = 1;
                     next->reqs.push_back(*it);
+                    // the camera vector may grow (and move) under a concurrent
+                    // vg_server_add_camera once the lock is released; the grid
+                    // itself lives until the camera has no pending frame
+                    next->reqs.back().grid = S->cams[it->camera].grid;
                     it = S->queue.erase(it);
                 }
                 next->busy = true;

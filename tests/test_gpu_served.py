@@ -167,3 +167,36 @@ def test_backpressure_and_latency_counters(vg):
     with pytest.raises(vg.VGError):
         s.submit(cam, np.zeros((800, 1400), np.float32), f.T_wc)   # larger than the server's frames
     s.close()
+
+
+def test_cameras_added_while_frames_are_served(vg):
+    # cameras admitted from one thread while another submits frames of
+    # earlier cameras: the server must keep serving every grid it admitted
+    # (its camera table grows meanwhile), and each grid must match the
+    # plain path
+    first = [make("robot", robot=70 + i, frames=3) for i in range(3)]
+    late = [make("robot", robot=80 + i, frames=1) for i in range(24)]
+    s = vg.Server(8 << 30, max_batch=4, queue_depth=3, pending_frames=12, plain_max=2)
+    cams = [_add(s, w) for w in first]
+    added = []
+
+    def adder():
+        for w in late:
+            added.append((_add(s, w), w))
+
+    th = threading.Thread(target=adder)
+    th.start()
+    tickets = []
+    for k in range(3):
+        for cam, w in zip(cams, first):
+            _submit_all(s, cam, type(w)(w.name, w.cam, w.grid, [w.frames[k]], w.prims), tickets)
+    th.join()
+    for cam, w in added:
+        _submit_all(s, cam, w, tickets)
+    assert all(s.wait(t) == vg.VG_OK for t in tickets)
+    for cam, w in list(zip(cams, first)) + added[:4]:
+        got, o = _read(s, cam, w)
+        want, ow = _plain(vg, w)
+        assert list(o) == list(ow) and np.array_equal(got, want)
+    assert s.stats()["cameras"] == len(first) + len(late)
+    s.close()
