@@ -399,8 +399,10 @@ VG_API int vg_server_submit(vg_server *server, int32_t camera, const void *depth
                             int32_t recentre, const double robot_pos_w[3], uint64_t *ticket);
 
 /* Waits up to timeout_us microseconds (negative: no limit) for a request.
- * Returns VG_OK when its launch completed, VG_ETIMEOUT if still pending,
- * VG_ECUDA or VG_EINVAL if it failed or is unknown. */
+ * Returns VG_OK when its frame's device work completed, VG_ETIMEOUT if still
+ * pending, VG_ECUDA or VG_EINVAL if it failed or is unknown.  A ticket's
+ * status stays queryable for the server's lifetime (one byte per ticket;
+ * the latencies behind vg_server_stats are kept until a reset). */
 VG_API int vg_server_wait(vg_server *server, uint64_t ticket, int64_t timeout_us);
 
 /* Waits for every queued frame of the camera, then copies its grid to dst
