@@ -32,6 +32,7 @@ static_assert(units::inflate_smem_words<3, 8, 8, 8>(3) <= (size_t)kDynWords, "in
 // twice the one-step kernel's, so that each CTA keeps more loads in flight
 constexpr int kMergeWords = kBatchMergeWords;
 static_assert(units::merge_shift_smem(kMergeWords) <= 4 * kDynWords, "merge-with-shift staging fits");
+static_assert(sizeof(FrameArgs) % 4 == 0, "frame arguments copy as words");
 
 __device__ __forceinline__ int find_item(const BatchItem *items, int n, int phase, int64_t u) {
     int lo = 0, hi = n - 1;
@@ -79,10 +80,18 @@ __device__ bool grid_sync(BatchCtl *ctl, unsigned nblocks) {
 }
 
 template <int LPR>
-__device__ __forceinline__ unsigned group_lpr(const BatchItem &it, const float S[3], const Box &b, int64_t grp,
-                                              int64_t G, uint32_t *box_fr, uint32_t *box_tr,
+__device__ __forceinline__ unsigned group_lpr(const FrameArgs &a, int buffered, const float S[3], const Box &b,
+                                              int64_t grp, int64_t G, uint32_t *box_fr, uint32_t *box_tr,
                                               const uint32_t *occ_box, uint32_t *buf) {
-    return rt_group<LPR, units::LoadL2>(it.a, S, b, grp, G, it.buffered, box_fr, box_tr, occ_box, buf);
+    return rt_group<LPR, units::LoadL2>(a, S, b, grp, G, buffered, box_fr, box_tr, occ_box, buf);
+}
+
+// Copies a frame's arguments into shared memory, by the threads of the CTA
+// (the caller places the barriers).
+__device__ __forceinline__ void stage_args(const FrameArgs &src, FrameArgs &dst) {
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(&src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(FrameArgs) / 4); k += kThreads) d[k] = __ldg(s + k);
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restrict__ items, BatchCtl *ctl) {
@@ -91,17 +100,32 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
     const int n = ctl->n;
     const unsigned nb = gridDim.x;
 
+    // The frame arguments of the unit at hand are staged in shared memory
+    // (s_a) whenever the CTA moves to another frame, so that the per-pixel
+    // and per-ray code reads them there rather than field by field from the
+    // table in global memory.
+    __shared__ FrameArgs s_a;
+    __shared__ int32_t s_kind;   // phase 1: dtype * 2 + vec; phase 3: LPR * 2 + buffered
+
     // ---- phase 1: voxelize ------------------------------------------------
-    for (int64_t u = blockIdx.x; u < ctl->total[0]; u += nb) {
-        const int i = find_item(items, n, 0, u);
-        const BatchItem &it = items[i];
-        const int64_t t = (u - it.off[0]) * kThreads + threadIdx.x;
-        if (it.dtype == 0) {
-            if (it.vec) units::voxelize_depth_thread<0, true>(it.a, t);
-            else units::voxelize_depth_thread<0, false>(it.a, t);
-        } else {
-            if (it.vec) units::voxelize_depth_thread<1, true>(it.a, t);
-            else units::voxelize_depth_thread<1, false>(it.a, t);
+    {
+        int cur = -1;
+        for (int64_t u = blockIdx.x; u < ctl->total[0]; u += nb) {
+            const int i = find_item(items, n, 0, u);   // the same for every thread
+            if (i != cur) {
+                __syncthreads();   // the previous frame's copy is no longer read
+                stage_args(items[i].a, s_a);
+                if (threadIdx.x == 0) s_kind = __ldg(&items[i].dtype) * 2 + __ldg(&items[i].vec);
+                __syncthreads();
+                cur = i;
+            }
+            const int64_t t = (u - __ldg(&items[i].off[0])) * kThreads + threadIdx.x;
+            switch (s_kind) {
+            case 0: units::voxelize_depth_thread<0, false>(s_a, t); break;
+            case 1: units::voxelize_depth_thread<0, true>(s_a, t); break;
+            case 2: units::voxelize_depth_thread<1, false>(s_a, t); break;
+            default: units::voxelize_depth_thread<1, true>(s_a, t); break;
+            }
         }
     }
     if (!grid_sync(ctl, nb)) return;
@@ -141,30 +165,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
         float S[3] = {0.0f, 0.0f, 0.0f};
         Box b = {0, 0, 0};
         for (int64_t u = lo; u < hi; ++u) {
-            const int i = find_item(items, n, 2, u);
-            const BatchItem &it = items[i];
+            const int i = find_item(items, n, 2, u);   // the same for every thread
             if (i != cur) {
-                if (cur >= 0) box_flush(items[cur].a, b, box_fr, box_tr);
+                if (cur >= 0) box_flush(s_a, b, box_fr, box_tr);   // ends with a barrier
+                else __syncthreads();   // phase 1's copy is no longer read
+                stage_args(items[i].a, s_a);
+                if (threadIdx.x == 0) s_kind = __ldg(&items[i].lpr) * 2 + __ldg(&items[i].buffered);
+                __syncthreads();
                 cur = i;
-                frame_start(it.a, S);
+                frame_start(s_a, S);
                 b = box_of(S);
-                box_stage<units::LoadL2>(it.a, b, box_fr, box_tr, occ_box);
+                box_stage<units::LoadL2>(s_a, b, box_fr, box_tr, occ_box);
             }
             // the frame's rays are spread over its G units of this phase
-            const int64_t grp = u - it.off[2];
-            const int64_t G = (i + 1 < n ? items[i + 1].off[2] : ctl->total[2]) - it.off[2];
+            const int64_t off = __ldg(&items[i].off[2]);
+            const int64_t grp = u - off;
+            const int64_t G = (i + 1 < n ? __ldg(&items[i + 1].off[2]) : ctl->total[2]) - off;
+            const int buffered = s_kind & 1;
             unsigned visits;
-            switch (it.lpr) {
-            case 8: visits = group_lpr<8>(it, S, b, grp, G, box_fr, box_tr, occ_box, dyn); break;
-            case 16: visits = group_lpr<16>(it, S, b, grp, G, box_fr, box_tr, occ_box, dyn); break;
-            default: visits = group_lpr<32>(it, S, b, grp, G, box_fr, box_tr, occ_box, dyn); break;
+            switch (s_kind >> 1) {
+            case 8: visits = group_lpr<8>(s_a, buffered, S, b, grp, G, box_fr, box_tr, occ_box, dyn); break;
+            case 16: visits = group_lpr<16>(s_a, buffered, S, b, grp, G, box_fr, box_tr, occ_box, dyn); break;
+            default: visits = group_lpr<32>(s_a, buffered, S, b, grp, G, box_fr, box_tr, occ_box, dyn); break;
             }
-            if (it.a.stats) {
+            if (s_a.stats) {
                 const unsigned total = __reduce_add_sync(kFull, visits);
-                if ((threadIdx.x & 31) == 0 && total) atomicAdd(it.a.stats + 2, (unsigned long long)total);
+                if ((threadIdx.x & 31) == 0 && total) atomicAdd(s_a.stats + 2, (unsigned long long)total);
             }
         }
-        if (cur >= 0) box_flush(items[cur].a, b, box_fr, box_tr);
+        if (cur >= 0) box_flush(s_a, b, box_fr, box_tr);
     }
     if (!grid_sync(ctl, nb)) return;
 
