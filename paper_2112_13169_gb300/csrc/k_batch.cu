@@ -26,6 +26,9 @@ namespace {
 
 using namespace rt;
 
+// loads of an inflate tile's staging issued together (fewer than the
+// one-step kernel's 8: this kernel's registers are capped at 64)
+constexpr int kInflateUnroll = 2;
 constexpr int kDynWords = kRtBuf * kThreads;   // also covers an inflate tile of radius <= 3
 static_assert(units::inflate_smem_words<3, 8, 8, 8>(3) <= (size_t)kDynWords, "inflate tile fits");
 // a merge with a pending re-centre takes units of kMergeWords plane words:
@@ -141,15 +144,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
         const PlaneGeom &g = it.a.g;
         if (it.txw == 8) {
             switch (it.a.r) {
-            case 1: units::inflate_tile<1, 8, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
-            case 2: units::inflate_tile<2, 8, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
-            default: units::inflate_tile<3, 8, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
+            case 1: units::inflate_tile<1, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
+            case 2: units::inflate_tile<2, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
+            default: units::inflate_tile<3, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
             }
         } else {
             switch (it.a.r) {
-            case 1: units::inflate_tile<1, 4, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
-            case 2: units::inflate_tile<2, 4, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
-            default: units::inflate_tile<3, 4, 8, 8, units::LoadL2>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
+            case 1: units::inflate_tile<1, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
+            case 2: units::inflate_tile<2, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
+            default: units::inflate_tile<3, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
             }
         }
     }

@@ -202,7 +202,7 @@ __host__ __device__ constexpr size_t inflate_smem_words(int r) {
 }
 
 // CTA-cooperative: every thread of the (256-thread) CTA must call this.
-template <int R, int TXW, int TY, int TZ, class L>
+template <int R, int TXW, int TY, int TZ, class L, int STAGE_UNROLL = 8>
 __device__ __forceinline__ void inflate_tile(const PlaneGeom &g, const uint32_t *raw, uint32_t *out, const int r_rt,
                                              int tile_x, int tile_y, int tile_z, uint32_t *sm) {
     const int r = R > 0 ? R : r_rt;
@@ -213,7 +213,7 @@ __device__ __forceinline__ void inflate_tile(const PlaneGeom &g, const uint32_t 
 
     // 1. stage raw words (zero outside the grid)
     const int n0 = hz * hy * hx;
-#pragma unroll 8
+#pragma unroll STAGE_UNROLL
     for (int i = threadIdx.x; i < n0; i += 256) {
         const int lx = i % hx, rest = i / hx, ly = rest % hy, lz = rest / hy;
         const int w = w0 + lx - 1, y = y0 + ly - r, z = z0 + lz - r;
