@@ -17,14 +17,17 @@ __global__ void __launch_bounds__(kThreads, 5) k_raytrace(const FrameArgs a, con
     frame_start(a, S);
     const Box b = box_of(S);
     const int64_t groups = rt_groups<LPR>(a);
-    // the first group's set-up needs only the pose, so it overlaps the
-    // end of K2; the occupancy is read after the wait (every CTA has a
-    // first group: the grid is no larger than the group count)
+    // the first group's set-up and walk need only the pose and the grid's
+    // shape, so they overlap the end of K2; the occupancy is read and the
+    // planes are marked after the wait (every CTA has a first group: the
+    // grid is no larger than the group count)
     Lane ln;
     rt_setup<LPR>(a, S, b, blockIdx.x, groups, ln);
+    box_clear(box_fr, box_tr);
+    const Pass1 p1 = rt_record(a, ln, b, buffered, buf);
     pdl_wait();
-    box_stage<units::LoadRO>(a, b, box_fr, box_tr, occ_box);
-    unsigned visits = rt_walk<LPR, units::LoadRO, EXACT>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
+    box_stage<units::LoadRO, false>(a, b, box_fr, box_tr, occ_box);
+    unsigned visits = rt_resolve<LPR, units::LoadRO, EXACT>(a, ln, b, p1, box_fr, box_tr, occ_box, buf);
     for (int64_t grp = blockIdx.x + gridDim.x; grp < groups; grp += gridDim.x)
         visits += rt_group<LPR, units::LoadRO, EXACT>(a, S, b, grp, groups, buffered, box_fr, box_tr, occ_box, buf);
     box_flush(a, b, box_fr, box_tr);

@@ -261,7 +261,7 @@ __device__ int walk_first_hit(const FrameArgs &a, const Ray &r, const int32_t n0
 }
 
 // Pass 2 of the two-pass walk: marks the slice's in-grid visits.  EXACT:
-// traced marks skip voxels the rays test as occupied (see rt_walk).
+// traced marks skip voxels the rays test as occupied (see rt_resolve).
 template <bool EXACT, class L>
 __device__ inline unsigned walk_marks(const FrameArgs &a, const Ray &r, const int32_t n0[3], bool visit_start,
                                float c_hi, const Box &b, int mode, int32_t hit_at, uint32_t *box_fr,
@@ -301,12 +301,16 @@ __device__ __forceinline__ Box box_of(const float S[3]) {
     return b;
 }
 
-template <class L>
+// CLEAR: also clear the box's marks (without it, box_clear has done so
+// earlier in the same CTA).
+template <class L, bool CLEAR = true>
 __device__ __forceinline__ void box_stage(const FrameArgs &a, const Box &b, uint32_t *box_fr, uint32_t *box_tr,
                                           uint32_t *occ_box) {
     for (int i = threadIdx.x; i < kBoxWords; i += kThreads) {
-        box_fr[i] = 0;
-        box_tr[i] = 0;
+        if (CLEAR) {
+            box_fr[i] = 0;
+            box_tr[i] = 0;
+        }
         const int32_t dw = i % kBoxW, dy = (i / kBoxW) % kBoxY, dz = i / (kBoxW * kBoxY);
         const int32_t wx = b.bw0 + dw, y = b.by0 + dy, z = b.bz0 + dz;
         uint32_t v = 0;
@@ -315,6 +319,15 @@ __device__ __forceinline__ void box_stage(const FrameArgs &a, const Box &b, uint
         occ_box[i] = v;
     }
     __syncthreads();
+}
+
+// Clears the box's marks only; the next box_stage<L, false> ends with the
+// barrier that makes the zeros visible to the CTA.
+__device__ __forceinline__ void box_clear(uint32_t *box_fr, uint32_t *box_tr) {
+    for (int i = threadIdx.x; i < kBoxWords; i += kThreads) {
+        box_fr[i] = 0;
+        box_tr[i] = 0;
+    }
 }
 
 // ORs the box's marks into the planes.  CTA-cooperative; starts with a
@@ -627,10 +640,34 @@ __device__ __forceinline__ void mark_visits(const FrameArgs &a, uint32_t *box_fr
     mark_flush(a, box_fr, box_tr, key, bits);
 }
 
-// The walk of one group of rays set up by rt_setup, by all threads of the
-// CTA; `buf` is this CTA's visit buffer (kRtBuf columns of kThreads words).
-// Returns this thread's in-grid visits.  Warp-synchronous (every lane of
-// every warp must call it; the CTA need not be in step).
+// What pass 1 leaves for the rest of a lane's walk.
+struct Pass1 {
+    int32_t nvis;   // visits recorded in the lane's buffer column
+    bool ovf;       // the slice does not fit the column: walk twice instead
+};
+
+// Pass 1 of a group's walk, by all threads of the CTA: each lane walks its
+// slice once and keeps its in-grid visits in its column of `buf` (box-packed
+// visits first, then plane bit indices).  Reads no global memory, so it may
+// run before the occupancy the visits are tested against is ready.
+// Warp-synchronous, like rt_walk.
+__device__ __forceinline__ Pass1 rt_record(const FrameArgs &a, const Lane &ln, const Box &b, int buffered,
+                                           uint32_t *buf) {
+    Pass1 p1{0, !buffered};
+    const bool visit_start = ln.j == 0 && !(a.lit & kLitSkipStart);
+    // (each phase starts with the warp reconverged, so that its lanes run
+    // the phase's loop together rather than in groups)
+    __syncwarp();
+    if (ln.active && !p1.ovf)
+        p1.ovf = !walk_record(ln.r, ln, ln.n0, visit_start, b, 32u * (uint32_t)a.g.wx, buf + threadIdx.x, p1.nvis);
+    __syncwarp();
+    return p1;
+}
+
+// The rest of a group's walk after rt_record: the first occupied visit of
+// each lane, the ray's first lane that met one, then the marks.  Returns
+// this thread's in-grid visits.  Warp-synchronous (every lane of every warp
+// must call it; the CTA need not be in step).
 // Traced marks after a ray's first occupied voxel are written without
 // re-reading the occupancy; a traced mark on an occupied voxel is then
 // overridden by K4's precedence.  That holds whenever the tested plane is a
@@ -638,9 +675,9 @@ __device__ __forceinline__ void mark_visits(const FrameArgs &a, uint32_t *box_fr
 // reading, whose resolve also puts traced above occupied) EXACT re-reads it
 // and leaves tested-occupied voxels unmarked, as Alg. 2 does.
 template <int LPR, class L, bool EXACT = false>
-__device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, const Box &b, int buffered,
-                                            uint32_t *box_fr, uint32_t *box_tr, const uint32_t *occ_box,
-                                            uint32_t *buf) {
+__device__ __forceinline__ unsigned rt_resolve(const FrameArgs &a, const Lane &ln, const Box &b, const Pass1 &p1,
+                                               uint32_t *box_fr, uint32_t *box_tr, const uint32_t *occ_box,
+                                               uint32_t *buf) {
     const int lane = threadIdx.x & 31;
     const int j = ln.j;
     const bool active = ln.active;
@@ -648,20 +685,14 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
     const float c_hi = ln.c_hi;
     const int32_t *n0 = ln.n0;
     const uint32_t R = 32u * (uint32_t)a.g.wx;
+    const uint32_t *col = buf + threadIdx.x;
+    const int32_t nvis = p1.nvis;
+    const bool ovf = p1.ovf;
+    const bool visit_start = j == 0 && !(a.lit & kLitSkipStart);
     unsigned visits = 0;
 
-    // ---- pass 1: walk the slice once, keep its in-grid visits --------
-    // (box-packed visits first, then plane bit indices), then find the
-    // first occupied one
-    // (each phase starts with the warp reconverged, so that its lanes run
-    // the phase's loop together rather than in groups)
-    uint32_t *col = buf + threadIdx.x;
-    int32_t nvis = 0, hit_at = -1;
-    bool ovf = !buffered;
-    const bool visit_start = j == 0 && !(a.lit & kLitSkipStart);
-    __syncwarp();
-    if (active && !ovf) ovf = !walk_record(r, ln, n0, visit_start, b, R, col, nvis);
-    __syncwarp();
+    // ---- first occupied visit of this lane -----------------------------
+    int32_t hit_at = -1;
     if (active && !ovf) hit_at = first_hit<L>(a, occ_box, col, nvis);
     if (active && ovf) hit_at = walk_first_hit<L>(a, r, n0, visit_start, c_hi, b, occ_box, R);
 
@@ -684,7 +715,7 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
         for (int q = 0; q < nvis; ++q) {
             if (mode == 1 && q == hit_at) continue;
             const bool traced = mode == 2 || (mode == 1 && q > hit_at);
-            const uint32_t p = buf[q * kThreads + threadIdx.x];
+            const uint32_t p = col[q * kThreads];
             if (EXACT && traced && ((occ_word<L>(a, occ_box, p) >> (p & 31u)) & 1u)) continue;
             marks_add(a, box_fr, box_tr, m, p, traced);
         }
@@ -694,6 +725,17 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
         visits += walk_marks<EXACT, L>(a, r, n0, visit_start, c_hi, b, mode, hit_at, box_fr, box_tr, occ_box, R);
     }
     return visits;
+}
+
+// The walk of one group of rays set up by rt_setup, by all threads of the
+// CTA; `buf` is this CTA's visit buffer (kRtBuf columns of kThreads words).
+// Returns this thread's in-grid visits.  Warp-synchronous.
+template <int LPR, class L, bool EXACT = false>
+__device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, const Box &b, int buffered,
+                                            uint32_t *box_fr, uint32_t *box_tr, const uint32_t *occ_box,
+                                            uint32_t *buf) {
+    const Pass1 p1 = rt_record(a, ln, b, buffered, buf);
+    return rt_resolve<LPR, L, EXACT>(a, ln, b, p1, box_fr, box_tr, occ_box, buf);
 }
 
 // One group of rays: rt_setup then rt_walk.
