@@ -323,8 +323,9 @@ __device__ __forceinline__ uint32_t merge4(uint32_t hi, uint32_t lo, uint32_t kn
 template <bool ALIGN8, class L, bool RAYS_LAST = false>
 __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl, uint8_t *loc, int64_t w) {
     if (w >= g.words) return;
-    const int32_t wxi = (int32_t)(w % g.wx);
-    const int64_t row = w / g.wx;
+    // rows are a power of two of words
+    const int32_t wxi = (int32_t)(w & (g.wx - 1));
+    const int64_t row = w >> (__ffs(g.wx) - 1);
     const int32_t x0 = wxi * 32;
     if (x0 >= g.nx) return;   // padding word, always zero
     const uint32_t oc = L::ld(pl.occ_inf + w), f = L::ld(pl.fr + w), t = L::ld(pl.tr + w);
@@ -389,14 +390,18 @@ __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Plane
     uint8_t *sm_out = sm + kVox + 32;     // results, 16-byte aligned
     const int tid = threadIdx.x;
     const int64_t rows = (int64_t)g.ny * g.nz;
+    // rows are a power of two of words, and so is WPU; grids have fewer
+    // than 2^31 voxels, so rows and voxel indices fit 32 bits
+    const int lw = __ffs(g.wx) - 1;
     int64_t b0, b1;
     if (g.wx <= WPU) {
-        const int64_t R = WPU / g.wx;
+        const int64_t R = WPU >> lw;
         const int64_t r0 = u * R, r1 = min(r0 + R, rows);
         b0 = r0 * g.nx;
         b1 = r1 * g.nx;
     } else {
-        const int64_t per = g.wx / WPU, row = u / per, xa = (u % per) * kVox;
+        const int lp = lw - (__ffs(WPU) - 1);   // log2 of the units per row
+        const int64_t row = u >> lp, xa = (u & ((int64_t(1) << lp) - 1)) * kVox;
         b0 = row * g.nx + min(xa, (int64_t)g.nx);
         b1 = row * g.nx + min(xa + kVox, (int64_t)g.nx);
     }
@@ -422,12 +427,12 @@ __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Plane
     for (int k = 0; k < WPU / 256; ++k) {
         // this thread's plane word and its 32 voxels
         const int64_t w = u * WPU + k * 256 + tid;
-        const int32_t x0 = (int32_t)(w % g.wx) * 32;
+        const int32_t x0 = (int32_t)(w & (g.wx - 1)) * 32;
         if (!(w < g.words && x0 < g.nx)) continue;
-        const int64_t row = w / g.wx;
-        const int32_t y = (int32_t)(row % g.ny), z = (int32_t)(row / g.ny);
+        const uint32_t row = (uint32_t)(w >> lw);
+        const int32_t y = (int32_t)(row % (uint32_t)g.ny), z = (int32_t)(row / (uint32_t)g.ny);
         const int nbits = min(32, g.nx - x0);
-        const int64_t d = row * g.nx + x0;
+        const int64_t d = (int64_t)row * g.nx + x0;
         const uint32_t oc = LP::ld(pl.occ_inf + w), f = LP::ld(pl.fr + w), t = LP::ld(pl.tr + w);
         const int32_t sy = y + dy, sz = z + dz, sx0 = x0 + dx;
         const bool row_ok = (unsigned)sy < (unsigned)g.ny && (unsigned)sz < (unsigned)g.nz;
