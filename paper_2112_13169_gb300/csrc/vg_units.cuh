@@ -134,7 +134,10 @@ __device__ __forceinline__ void voxelize_depth_thread(const FrameArgs &a, int64_
         }
     }
     uint32_t key[4], bit[4];
-    int32_t v = (int32_t)(p0 / a.W), u = (int32_t)(p0 - (int64_t)v * a.W);
+    // images hold fewer than 2^31 pixels, so p0 (at most 1023 past the last
+    // one) fits 32 bits
+    const uint32_t q0 = (uint32_t)p0;
+    int32_t v = (int32_t)(q0 / (uint32_t)a.W), u = (int32_t)(q0 - (uint32_t)v * (uint32_t)a.W);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         key[j] = kNoWord;
@@ -529,9 +532,10 @@ __device__ __forceinline__ void shift_chunk(const PlaneGeom &g, int32_t dx, int3
     const int64_t i0 = chunk * 16;
     if (i0 >= g.nvox) return;
     const int64_t off = (int64_t)dx + (int64_t)dy * g.nx + (int64_t)dz * g.nx * g.ny;
-    int32_t x = (int32_t)(i0 % g.nx);
-    int64_t yz = i0 / g.nx;
-    int32_t y = (int32_t)(yz % g.ny), z = (int32_t)(yz / g.ny);
+    // grids hold fewer than 2^31 voxels: 32-bit division
+    const uint32_t yz = (uint32_t)i0 / (uint32_t)g.nx;
+    int32_t x = (int32_t)((uint32_t)i0 - yz * (uint32_t)g.nx);
+    int32_t y = (int32_t)(yz % (uint32_t)g.ny), z = (int32_t)(yz / (uint32_t)g.ny);
     // which of the 16 voxels have a source voxel
     uint32_t valid = 0;
 #pragma unroll
