@@ -6,14 +6,16 @@
 //   phase 2  K2 inflate            8 x 8 x 8-word tiles (radius 1..3)
 //   phase 3  K3 ray trace          groups of at most 256 / LPR rays (a
 //                                  frame's rays spread over its units)
-//   phase 4  K4 merge              256 plane words
+//   phase 4  K4 merge              256 plane words (512 with a pending
+//                                  re-centre)
 // with a grid-wide barrier between phases.  A frame's re-centre (K5) is not
 // a phase: it is left pending on its grid and applied by that grid's next
-// merge, which then writes the whole grid out of place (merge_shift_word).  Units of every frame are laid
-// end to end per phase (BatchItem::off), so a CTA picks a unit, finds its
-// frame by binary search and runs the same device code as the one-step
-// kernels (vg_units.cuh, vg_rt.cuh).  Reads of data an earlier phase wrote
-// skip the L1 (LoadL2).
+// merge, which then writes the whole grid out of place (merge_shift_unit).
+// Units of every frame are laid end to end per phase (BatchItem::off).  A
+// CTA finds the frame of its first unit of a phase by binary search, steps
+// forward through the frames as its units advance (see run_begin), and runs
+// the same device code as the one-step kernels (vg_units.cuh, vg_rt.cuh).
+// Reads of data an earlier phase wrote skip the L1 (LoadL2).
 //
 // The barrier waits with a clock64 deadline: if the other CTAs do not all
 // arrive within a few seconds, the waiting CTA sets BatchCtl::error and
@@ -45,6 +47,21 @@ __device__ __forceinline__ int find_item(const BatchItem *items, int n, int phas
         else hi = mid - 1;
     }
     return lo;
+}
+
+// In the voxelize and ray-trace phases a CTA's units are a contiguous run
+// [lo, hi) of the phase's units, so that it moves to another frame (and
+// restages that frame's arguments) only a few times.  Their units cost about
+// the same in every frame.  The inflate and merge units cost more in some
+// frames than in others (tile width and radius; a merge with or without a
+// re-centre), so there the units go round the CTAs in turn.
+__device__ __forceinline__ int64_t run_begin(int64_t total, unsigned b, unsigned nb) { return total * b / nb; }
+
+// The frame of unit u, given the frame i of an earlier unit of the same CTA
+// in the same phase (frames with no units in this phase are skipped).
+__device__ __forceinline__ int next_item(const BatchItem *items, int n, int phase, int64_t u, int i) {
+    while (i + 1 < n && __ldg(&items[i + 1].off[phase]) <= u) ++i;
+    return i;
 }
 
 // Grid-wide barrier with a deadline.  Returns false (for every thread of
@@ -113,8 +130,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
     // ---- phase 1: voxelize ------------------------------------------------
     {
         int cur = -1;
-        for (int64_t u = blockIdx.x; u < ctl->total[0]; u += nb) {
-            const int i = find_item(items, n, 0, u);   // the same for every thread
+        const int64_t lo = run_begin(ctl->total[0], blockIdx.x, nb), hi = run_begin(ctl->total[0], blockIdx.x + 1, nb);
+        int i = find_item(items, n, 0, lo);
+        for (int64_t u = lo; u < hi; ++u) {
+            i = next_item(items, n, 0, u, i);   // the same for every thread
             if (i != cur) {
                 __syncthreads();   // the previous frame's copy is no longer read
                 stage_args(items[i].a, s_a);
@@ -134,25 +153,32 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
     if (!grid_sync(ctl, nb)) return;
 
     // ---- phase 2: inflate -------------------------------------------------
-    for (int64_t u = blockIdx.x; u < ctl->total[1]; u += nb) {
-        const int i = find_item(items, n, 1, u);
-        const BatchItem &it = items[i];
-        const int64_t local = u - it.off[1];
-        const int tx = (int)(local % it.tiles[0]);
-        const int ty = (int)((local / it.tiles[0]) % it.tiles[1]);
-        const int tz = (int)(local / ((int64_t)it.tiles[0] * it.tiles[1]));
-        const PlaneGeom &g = it.a.g;
-        if (it.txw == 8) {
-            switch (it.a.r) {
-            case 1: units::inflate_tile<1, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
-            case 2: units::inflate_tile<2, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
-            default: units::inflate_tile<3, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
-            }
-        } else {
-            switch (it.a.r) {
-            case 1: units::inflate_tile<1, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
-            case 2: units::inflate_tile<2, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
-            default: units::inflate_tile<3, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
+    {
+        // units in turn over the CTAs: their cost differs between frames,
+        // and interleaving keeps the CTAs' shares even
+        int i = find_item(items, n, 1, blockIdx.x);
+        for (int64_t u = blockIdx.x; u < ctl->total[1]; u += nb) {
+            i = next_item(items, n, 1, u, i);
+            const BatchItem &it = items[i];
+            // a frame has fewer than 2^27 plane words, so fewer tiles
+            const uint32_t local = (uint32_t)(u - it.off[1]), t0 = (uint32_t)it.tiles[0];
+            const uint32_t t01 = local / t0;
+            const int tx = (int)(local - t01 * t0);
+            const int ty = (int)(t01 % (uint32_t)it.tiles[1]);
+            const int tz = (int)(t01 / (uint32_t)it.tiles[1]);
+            const PlaneGeom &g = it.a.g;
+            if (it.txw == 8) {
+                switch (it.a.r) {
+                case 1: units::inflate_tile<1, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
+                case 2: units::inflate_tile<2, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
+                default: units::inflate_tile<3, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
+                }
+            } else {
+                switch (it.a.r) {
+                case 1: units::inflate_tile<1, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
+                case 2: units::inflate_tile<2, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
+                default: units::inflate_tile<3, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
+                }
             }
         }
     }
@@ -162,13 +188,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
     // a contiguous run of units per CTA, so the camera box is staged again
     // only when the run crosses into another frame
     {
-        const int64_t total = ctl->total[2];
-        const int64_t lo = total * blockIdx.x / nb, hi = total * (blockIdx.x + 1) / nb;
-        int cur = -1;
+        const int64_t lo = run_begin(ctl->total[2], blockIdx.x, nb), hi = run_begin(ctl->total[2], blockIdx.x + 1, nb);
+        int cur = -1, i = find_item(items, n, 2, lo);
         float S[3] = {0.0f, 0.0f, 0.0f};
         Box b = {0, 0, 0};
         for (int64_t u = lo; u < hi; ++u) {
-            const int i = find_item(items, n, 2, u);   // the same for every thread
+            i = next_item(items, n, 2, u, i);   // the same for every thread
             if (i != cur) {
                 if (cur >= 0) box_flush(s_a, b, box_fr, box_tr);   // ends with a barrier
                 else __syncthreads();   // phase 1's copy is no longer read
@@ -201,15 +226,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
     if (!grid_sync(ctl, nb)) return;
 
     // ---- phase 4: merge ---------------------------------------------------
-    for (int64_t u = blockIdx.x; u < ctl->total[3]; u += nb) {
-        const int i = find_item(items, n, 3, u);
-        const BatchItem &it = items[i];
-        const int64_t w = (u - it.off[3]) * kThreads + threadIdx.x;
-        if (it.loc_dst)
-            units::merge_shift_unit<kMergeWords, units::LoadL2, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, it.loc_dst, it.dx, it.dy, it.dz,
-                                                   u - it.off[3], reinterpret_cast<uint8_t *>(dyn));
-        else if (it.align8) units::merge_word<true, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
-        else units::merge_word<false, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
+    {
+        // units in turn over the CTAs: their cost differs between frames,
+        // and interleaving keeps the CTAs' shares even
+        int i = find_item(items, n, 3, blockIdx.x);
+        for (int64_t u = blockIdx.x; u < ctl->total[3]; u += nb) {
+            i = next_item(items, n, 3, u, i);
+            const BatchItem &it = items[i];
+            const int64_t w = (u - it.off[3]) * kThreads + threadIdx.x;
+            if (it.loc_dst)
+                units::merge_shift_unit<kMergeWords, units::LoadL2, units::LoadL2>(
+                    it.a.g, it.a.pl, it.a.loc, it.loc_dst, it.dx, it.dy, it.dz, u - it.off[3],
+                    reinterpret_cast<uint8_t *>(dyn));
+            else if (it.align8) units::merge_word<true, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
+            else units::merge_word<false, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
+        }
     }
 }
 
