@@ -316,33 +316,33 @@ VG_API int vg_batch_autotune(vg_batch *batch, const vg_frame *frames, int32_t n,
 
 /*
  * Served form: a request loop for many cameras with continuous batching.
- * A server owns one grid per admitted camera (all resident on the device),
- * a pinned host pool for submitted frames and device staging for the frames
- * of the launches in flight.  A server thread forms batches from the queued
+ * A server owns one grid per admitted camera (all resident on the device)
+ * and a device pool for submitted frames.  A server thread forms batches from the queued
  * requests -- oldest first, at most one frame per camera per launch, so the
  * frames of one camera apply in submission order -- and issues each batch
  * in one of two ways.  A batch of at most plain_max frames runs each frame
  * as the per-frame kernel chain of vg_integrate_depth on one of several
- * streams (a camera always on the same one), K1 reading the frame in place
- * from the pinned pool, so the frames of different cameras overlap on the
- * device.  A larger batch has its depth copied to the device on a copy
- * stream and runs as one fused launch (as vg_batch_step); fused launches
- * are ordered after all earlier work of the server and before all later
- * work.  Requests that arrive while launches are on the GPU join the next
+ * streams (a camera always on the same one), so the frames of different
+ * cameras overlap on the device.  A larger batch runs as one fused launch
+ * (as vg_batch_step); fused launches are ordered after all earlier work of
+ * the server and before all later work.  Both read the frames from the
+ * pool.  Requests that arrive while launches are on the GPU join the next
  * launch as soon as a launch slot frees up.  While launches are in flight
  * the server thread polls their completion events (it keeps one CPU core
  * busy meanwhile) and stamps each frame's completion as it is seen.  Every
  * entry point is thread-safe.
  *
- *  memory_budget  bytes of device memory the server may hold: its staging
- *                 and tables plus the grids of the cameras it admits.
+ *  memory_budget  bytes of device memory the server may hold: its frame
+ *                 pool (pending_frames frames of max_width x max_height x 4
+ *                 bytes, each rounded up to 256) and launch tables plus the
+ *                 grids of the cameras it admits.
  *  max_batch      frames per launch (1 .. 4096).
  *  max_width, max_height
  *                 the largest depth frame a camera may submit.
  *  queue_depth    launches on the GPU at once (1 .. 8); 2 or more overlap
- *                 a launch with the next one's copies or kernels.
- *  pending_frames submitted frames the host pool holds (queued or in
- *                 flight) before vg_server_submit reports VG_EBUSY.
+ *                 a launch with the next one's kernels.
+ *  pending_frames submitted frames the pool holds (queued or in flight)
+ *                 before vg_server_submit reports VG_EBUSY.
  *  plain_max      the largest batch issued as per-frame kernel chains
  *                 (0 .. 4096; 0 selects the default, 4); larger batches
  *                 run as one fused launch.  Results do not depend on it.
@@ -362,7 +362,7 @@ typedef struct {
     double latency_p50_us;    /* submission to the moment the frame's device work is seen to end */
     double latency_p99_us;
     double latency_max_us;
-    int64_t bytes_in_use;     /* device bytes held (staging, tables, grids) */
+    int64_t bytes_in_use;     /* device bytes held (frame pool, tables, grids) */
     int32_t cameras;
 } vg_server_stats_t;
 
@@ -387,12 +387,14 @@ VG_API int vg_server_add_camera(vg_server *server, const vg_params *params, cons
 VG_API int vg_server_remove_camera(vg_server *server, int32_t camera);
 
 /*
- * Queues one frame of a camera: depth is host memory (W x H, dtype as for
- * vg_integrate_depth) and is copied into the server's pool before the call
- * returns.  recentre != 0 re-centres the grid on robot_pos_w after the
+ * Queues one frame of a camera: depth is host memory, pageable or
+ * page-locked (W x H, dtype as for vg_integrate_depth).  It is copied into
+ * the server's device pool, and that copy has ended when the call returns,
+ * so the caller may reuse the buffer at once.  recentre != 0 re-centres the grid on robot_pos_w after the
  * merge.  *ticket (may be NULL) identifies the request.
  * Errors: VG_EINVAL (bad argument, frame larger than max_width x max_height,
- * unknown or removed camera), VG_EBUSY (the pool is full: retry later).
+ * unknown or removed camera), VG_EBUSY (the pool is full: retry later),
+ * VG_ECUDA (the copy failed; nothing was queued).
  */
 VG_API int vg_server_submit(vg_server *server, int32_t camera, const void *depth, int32_t width,
                             int32_t height, int32_t dtype, float depth_scale, const double T_wc[16],

@@ -1,8 +1,10 @@
 // vg_server.cu -- the served form: continuous batching of measurements from
 // many cameras (declared in include/vg.h).
 //
-// Client threads submit frames (copied into a pinned host pool) into one
-// arrival-ordered queue.  The server thread repeatedly
+// Client threads submit frames into one arrival-ordered queue.  Each frame
+// is copied from the caller's host memory (pageable or page-locked) into a
+// slot of a device pool on one of a few copy streams, and the submit
+// returns once that copy has ended.  The server thread repeatedly
 //   - polls the completion events of the launches in flight, stamping each
 //     frame's completion time as soon as its work has ended, and retires a
 //     launch (status, latencies, pool slots, launch slot) once all of its
@@ -12,11 +14,10 @@
 //   - issues the batch in one of two ways:
 //       small batches (at most plain_max frames): each frame runs the
 //       per-frame kernel chain (K1..K4, PDL-chained) on its camera's lane
-//       stream, K1 reading the frame in place from the pinned pool over the
-//       host link; frames of different cameras overlap on the device;
-//       larger batches: the depth frames are copied to device staging on
-//       the copy stream and the batch runs as one fused cooperative launch
-//       (vg_batch_prepare + vg_batch_enqueue) on the fused stream.
+//       stream, K1 reading the frame from its pool slot; frames of
+//       different cameras overlap on the device;
+//       larger batches: one fused cooperative launch (vg_batch_prepare +
+//       vg_batch_enqueue) on the fused stream, reading the pool slots too.
 // Frames of one camera apply in submission order: one per launch, launches
 // issued in order, a camera always on the same lane stream, and every fused
 // launch fenced both ways against the lanes (it waits for the lanes' work
@@ -27,13 +28,15 @@
 // While launches are in flight the server thread spins on their events
 // (cudaEventQuery) instead of sleeping, so a completion is seen within
 // microseconds; with nothing in flight it sleeps on the condition variable.
-// The mutex is never held across a CUDA call, and the server's streams are
+// The server's mutex is never held across a CUDA call (a copy stream's own
+// mutex is, for one submit's copy), and the server's streams are
 // non-blocking so a synchronous copy elsewhere does not wait for them.
 #include "vg.h"
 
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -51,6 +54,9 @@ using Clock = std::chrono::steady_clock;
 constexpr int kLanes = 8;
 // Default largest batch issued as per-frame chains (vg_server_params.plain_max == 0).
 constexpr int kDefaultPlainMax = 4;
+// Streams that copy submitted frames into the pool; concurrent submits take
+// them in turn.
+constexpr int kCopyStreams = 4;
 
 struct Request {
     uint64_t ticket;
@@ -74,8 +80,6 @@ struct Camera {
 
 struct Launch {
     vg_batch *batch = nullptr;
-    uint8_t *staging = nullptr;   // max_batch frames of device staging (fused launches)
-    cudaEvent_t copied = nullptr;
     cudaEvent_t done = nullptr;   // end of a fused launch
     std::vector<cudaEvent_t> ev;  // end of each frame's chain (per-frame launches)
     std::vector<Request> reqs;
@@ -92,13 +96,16 @@ struct vg_server {
     int plain_max = kDefaultPlainMax;
     int device = 0;
     size_t frame_bytes = 0;
-    cudaStream_t compute = nullptr, copy = nullptr, admin = nullptr;
+    cudaStream_t compute = nullptr, admin = nullptr;
+    cudaStream_t copies[kCopyStreams] = {};
+    std::mutex copy_mu[kCopyStreams];     // one submit at a time per copy stream
+    std::atomic<unsigned> next_copy{0};
     cudaStream_t lanes[kLanes] = {};
     cudaEvent_t lane_tail[kLanes] = {};   // a lane's work before a fused launch
     bool lane_dirty[kLanes] = {};         // work issued on the lane since the last fused fence
     bool lane_behind[kLanes] = {};        // a fused launch was issued since the lane's last work
     cudaEvent_t fused_tail = nullptr;     // end of the last fused launch
-    uint8_t *pinned = nullptr;
+    uint8_t *slots = nullptr;             // device pool: pending_frames frames of frame_bytes
     std::vector<int32_t> free_slots;
     std::vector<Camera> cams;
     std::deque<Request> queue;
@@ -172,9 +179,8 @@ void poll(Launch &L) {
     }
 }
 
-// Per-frame chains: each frame on its camera's lane, K1 reading the pinned
-// pool slot in place.  A frame whose work could not be enqueued ends now
-// with its error.
+// Per-frame chains: each frame on its camera's lane, K1 reading its pool
+// slot.  A frame whose work could not be enqueued ends now with its error.
 void issue_lanes(vg_server *S, Launch &L) {
     for (size_t k = 0; k < L.reqs.size(); ++k) {
         Request &r = L.reqs[k];
@@ -188,7 +194,7 @@ void issue_lanes(vg_server *S, Launch &L) {
         S->lane_dirty[lane] = true;
         vg_grid *grid = r.grid;
         if (rc == VG_OK)
-            rc = vg_integrate_depth(grid, S->pinned + (size_t)r.slot * S->frame_bytes, VG_MEM_HOST, r.width,
+            rc = vg_integrate_depth(grid, S->slots + (size_t)r.slot * S->frame_bytes, VG_MEM_DEVICE, r.width,
                                     r.height, r.dtype, r.scale, r.T_wc, st);
         if (rc == VG_OK && r.recentre) rc = vg_shift(grid, r.pos, st);
         if (rc == VG_OK && cudaEventRecord(L.ev[k], st) != cudaSuccess) rc = VG_ECUDA;
@@ -206,22 +212,13 @@ int issue_fused(vg_server *S, Launch &L) {
             return VG_ECUDA;
         S->lane_dirty[i] = false;
     }
-    for (size_t k = 0; k < n; ++k) {
-        const Request &r = L.reqs[k];
-        const size_t bytes = (size_t)r.width * r.height * (r.dtype == VG_DEPTH_F32 ? 4 : 2);
-        cudaError_t e = cudaMemcpyAsync(L.staging + k * S->frame_bytes, S->pinned + (size_t)r.slot * S->frame_bytes,
-                                        bytes, cudaMemcpyHostToDevice, S->copy);
-        if (e != cudaSuccess) return VG_ECUDA;
-    }
-    if (cudaEventRecord(L.copied, S->copy) != cudaSuccess) return VG_ECUDA;
-    if (cudaStreamWaitEvent(S->compute, L.copied, 0) != cudaSuccess) return VG_ECUDA;
     std::vector<vg_frame> fr(n);
     for (size_t k = 0; k < n; ++k) {
         const Request &r = L.reqs[k];
         vg_frame &f = fr[k];
         std::memset(&f, 0, sizeof(f));
         f.grid = r.grid;
-        f.depth = L.staging + k * S->frame_bytes;
+        f.depth = S->slots + (size_t)r.slot * S->frame_bytes;
         f.width = r.width;
         f.height = r.height;
         f.dtype = r.dtype;
@@ -248,9 +245,7 @@ void issue(vg_server *S, Launch &L) {
     }
     const int rc = issue_fused(S, L);
     if (rc != VG_OK) {
-        // nothing of this batch is waited for: end it here, once the
-        // copies that did start have ended
-        cudaStreamSynchronize(S->copy);
+        // nothing of this batch is waited for: end it here
         const Clock::time_point now = Clock::now();
         for (Request &r : L.reqs) end_frame(r, rc, now, L.remaining);
     }
@@ -328,30 +323,29 @@ int vg_server_create(const vg_server_params *p, vg_server **out) {
     S->p = *p;
     S->plain_max = p->plain_max ? p->plain_max : kDefaultPlainMax;
     S->frame_bytes = ((size_t)p->max_width * p->max_height * 4 + 255) & ~size_t(255);
-    const size_t staging = S->frame_bytes * (size_t)p->max_batch;
-    // staging and a generous bound on each launch's descriptor table
-    S->fixed_bytes = (int64_t)(staging + (size_t)p->max_batch * 1024 + 4096) * p->queue_depth;
+    // the frame pool and a generous bound on each launch's descriptor table
+    S->fixed_bytes = (int64_t)(S->frame_bytes * (size_t)p->pending_frames) +
+                     (int64_t)((size_t)p->max_batch * 1024 + 4096) * p->queue_depth;
     if (S->fixed_bytes > p->memory_budget) {
         delete S;
         return VG_ENOMEM;
     }
     cudaError_t e = cudaGetDevice(&S->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking);
+    for (int i = 0; i < kCopyStreams && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithFlags(&S->copies[i], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->admin, cudaStreamNonBlocking);
     for (int i = 0; i < kLanes && e == cudaSuccess; ++i) {
         e = cudaStreamCreateWithFlags(&S->lanes[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->lane_tail[i], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->fused_tail, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&S->pinned, S->frame_bytes * (size_t)p->pending_frames);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->slots, S->frame_bytes * (size_t)p->pending_frames);
     int rc = e == cudaSuccess ? VG_OK : (e == cudaErrorMemoryAllocation ? VG_ENOMEM : VG_ECUDA);
     S->launches.resize((size_t)p->queue_depth);
     for (Launch &L : S->launches) {
         if (rc != VG_OK) break;
         rc = vg_batch_create(p->max_batch, &L.batch);
-        if (rc == VG_OK && cudaMalloc((void **)&L.staging, staging) != cudaSuccess) rc = VG_ENOMEM;
-        if (rc == VG_OK && cudaEventCreateWithFlags(&L.copied, cudaEventDisableTiming) != cudaSuccess) rc = VG_ECUDA;
         if (rc == VG_OK && cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) rc = VG_ECUDA;
         const int nev = std::min(S->plain_max, p->max_batch);
         for (int k = 0; k < nev && rc == VG_OK; ++k) {
@@ -387,13 +381,10 @@ void vg_server_destroy(vg_server *S) {
     }
     cudaSetDevice(S->device);
     if (S->compute) cudaStreamSynchronize(S->compute);
-    if (S->copy) cudaStreamSynchronize(S->copy);
     for (int i = 0; i < kLanes; ++i)
         if (S->lanes[i]) cudaStreamSynchronize(S->lanes[i]);
     for (Launch &L : S->launches) {
         vg_batch_destroy(L.batch);
-        cudaFree(L.staging);
-        if (L.copied) cudaEventDestroy(L.copied);
         if (L.done) cudaEventDestroy(L.done);
         for (cudaEvent_t ev : L.ev) cudaEventDestroy(ev);
     }
@@ -404,9 +395,10 @@ void vg_server_destroy(vg_server *S) {
     if (S->fused_tail) cudaEventDestroy(S->fused_tail);
     for (Camera &c : S->cams)
         if (c.grid) vg_destroy(c.grid);
-    cudaFreeHost(S->pinned);
+    cudaFree(S->slots);
     if (S->compute) cudaStreamDestroy(S->compute);
-    if (S->copy) cudaStreamDestroy(S->copy);
+    for (int i = 0; i < kCopyStreams; ++i)
+        if (S->copies[i]) cudaStreamDestroy(S->copies[i]);
     if (S->admin) cudaStreamDestroy(S->admin);
     delete S;
 }
@@ -483,9 +475,31 @@ int vg_server_submit(vg_server *S, int32_t camera, const void *depth, int32_t wi
         S->free_slots.pop_back();
         ++S->cams[camera].pending;   // keeps the camera alive while the frame is copied in
     }
+    // the frame goes straight into its device slot, whether the caller's
+    // memory is pageable or page-locked, and the call returns once the copy
+    // has ended, so the caller may reuse its buffer at once
     const size_t bytes = (size_t)width * height * (dtype == VG_DEPTH_F32 ? 4 : 2);
-    std::memcpy(S->pinned + (size_t)r.slot * S->frame_bytes, depth, bytes);
+    cudaError_t e = cudaSuccess;
+    {
+        int prev = -1;
+        e = cudaGetDevice(&prev);
+        if (e == cudaSuccess && prev != S->device) e = cudaSetDevice(S->device);
+        const unsigned c = S->next_copy.fetch_add(1u, std::memory_order_relaxed) % kCopyStreams;
+        if (e == cudaSuccess) {
+            std::lock_guard<std::mutex> cg(S->copy_mu[c]);
+            e = cudaMemcpyAsync(S->slots + (size_t)r.slot * S->frame_bytes, depth, bytes, cudaMemcpyHostToDevice,
+                                S->copies[c]);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(S->copies[c]);
+        }
+        if (prev >= 0 && prev != S->device) cudaSetDevice(prev);
+    }
     std::lock_guard<std::mutex> g(S->mu);
+    if (e != cudaSuccess) {
+        S->free_slots.push_back(r.slot);
+        --S->cams[camera].pending;
+        S->cv.notify_all();
+        return VG_ECUDA;
+    }
     r.ticket = S->status.size();
     S->status.push_back(0);
     ++S->submitted;

@@ -131,8 +131,9 @@ def test_admission_by_memory_budget(vg):
     w = make("robot", robot=50, frames=1)
     g = w.grid
     per_grid = vg.vg_grid_bytes(vg.make_params(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf))
-    # the server's own staging (2 launches x 4 frames of 1280x720x4) plus room for two grids
-    fixed = 2 * (4 * ((1280 * 720 * 4 + 255) // 256 * 256) + 4 * 1024 + 4096)
+    # the server's own frame pool (16 pending frames of 1280x720x4, the
+    # default 4 x max_batch) and 2 launch tables, plus room for two grids
+    fixed = 16 * ((1280 * 720 * 4 + 255) // 256 * 256) + 2 * (4 * 1024 + 4096)
     s = vg.Server(fixed + 2 * per_grid + per_grid // 2, max_batch=4)
     a = _add(s, w)
     b = _add(s, w)
@@ -199,4 +200,36 @@ def test_cameras_added_while_frames_are_served(vg):
         want, ow = _plain(vg, w)
         assert list(o) == list(ow) and np.array_equal(got, want)
     assert s.stats()["cameras"] == len(first) + len(late)
+    s.close()
+
+
+@pytest.mark.parametrize("page_locked", [False, True], ids=["pageable", "page-locked"])
+def test_caller_may_reuse_its_buffer_when_submit_returns(vg, page_locked):
+    # a submit copies the frame before it returns: the client overwrites its
+    # one buffer with the next frame (or garbage) at once, and the grid must
+    # still match the plain path, whether the buffer is pageable or
+    # page-locked (a copy from page-locked memory would otherwise still be
+    # in flight)
+    w = make("robot", robot=90, frames=4)
+    s = vg.Server(4 << 30, max_batch=4, queue_depth=2, pending_frames=8)
+    cam = _add(s, w)
+    shape, dt = w.frames[0].depth.shape, w.frames[0].depth.dtype
+    if page_locked:
+        buf = torch.empty(shape, dtype=torch.float32 if dt == np.float32 else torch.uint16).pin_memory().numpy()
+    else:
+        buf = np.empty(shape, dt)
+    tickets = []
+    for f in w.frames:
+        np.copyto(buf, f.depth)
+        while True:
+            t = s.submit(cam, buf, f.T_wc, f.robot_pos, w.cam.scale)
+            if t is not None:
+                break
+            threading.Event().wait(0.001)
+        tickets.append(t)
+        buf.fill(0.5 if dt == np.float32 else 7)   # the caller's next use of its buffer
+    assert all(s.wait(t) == vg.VG_OK for t in tickets)
+    got, o = _read(s, cam, w)
+    want, ow = _plain(vg, w)
+    assert list(o) == list(ow) and np.array_equal(got, want)
     s.close()
