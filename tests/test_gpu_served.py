@@ -204,13 +204,14 @@ def test_cameras_added_while_frames_are_served(vg):
 
 
 @pytest.mark.parametrize("page_locked", [False, True], ids=["pageable", "page-locked"])
-def test_caller_may_reuse_its_buffer_when_submit_returns(vg, page_locked):
+@pytest.mark.parametrize("robot", [89, 90], ids=["320x240", "848x480"])
+def test_caller_may_reuse_its_buffer_when_submit_returns(vg, page_locked, robot):
     # a submit copies the frame before it returns: the client overwrites its
     # one buffer with the next frame (or garbage) at once, and the grid must
     # still match the plain path, whether the buffer is pageable or
     # page-locked (a copy from page-locked memory would otherwise still be
     # in flight)
-    w = make("robot", robot=90, frames=4)
+    w = make("robot", robot=robot, frames=4)
     s = vg.Server(4 << 30, max_batch=4, queue_depth=2, pending_frames=8)
     cam = _add(s, w)
     shape, dt = w.frames[0].depth.shape, w.frames[0].depth.dtype
