@@ -147,6 +147,19 @@ def test_lanes_on_full_size_sequence(vg):
         run_workload(vg, make("seq", frames=2), 2, lanes=lanes)
 
 
+def test_long_rays_take_more_lanes(vg):
+    # 0.02 m voxels and a 5 m range: 250 voxels deep, so the automatic
+    # choice gives each ray 32 lanes (a slice of 8 or 16 lanes would not fit
+    # the visit buffer), and rays cross a 200 x 160 x 90 grid and leave it
+    rng = np.random.default_rng(41)
+    P = Pair(vg, (200, 160, 90), 0.02, 87.0, 58.0, 5.0, 2, (0.01, -0.02, 0.03))
+    for k in range(2):
+        d = rng.uniform(0.8, 5.5, size=(48, 64)).astype(np.float32)
+        d[rng.random(d.shape) < 0.15] = 0
+        P.depth(d, body_pose([0.01, -0.02, 0.03], rng.uniform(-np.pi, np.pi), rng.uniform(-0.3, 0.3)))
+    P.close()
+
+
 def test_huge_plane_takes_the_unbuffered_walk(vg):
     # 1 x 4096 x 4096 voxels: 2^26 plane words, too many for a packed visit,
     # so every lane walks twice instead of buffering
