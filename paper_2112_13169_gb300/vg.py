@@ -158,6 +158,7 @@ def make_params(n, vox_size, fov_x_deg, fov_y_deg, depth, vox_inf, flags=0):
 _TORCH = None
 _TORCH_DTYPES = None
 _CUDA = None
+_CURRENT_STREAM = None   # () -> torch's current cudaStream_t on the current device, as an int
 
 
 def _torch():
@@ -174,14 +175,28 @@ def _torch():
     return _TORCH or None
 
 
+def _current_stream_getter(t):
+    """torch's current stream as an int.  torch.cuda.current_stream() builds a
+    Stream object on every call (about 3 us on a Grace core); the raw getter
+    that torch's own generated code uses returns the handle directly, and the
+    public call is the fallback where it is missing."""
+    raw = getattr(t._C, "_cuda_getCurrentRawStream", None)
+    if raw is None:
+        return lambda: t.cuda.current_stream().cuda_stream
+    device = t.cuda.current_device
+    return lambda: raw(device())
+
+
 def _stream(stream):
     """The cudaStream_t (an integer) to pass for `stream`."""
-    global _CUDA
+    global _CUDA, _CURRENT_STREAM
     if stream is None:
-        t = _torch()
         if _CUDA is None:
+            t = _torch()
             _CUDA = bool(t is not None and t.cuda.is_available())
-        return t.cuda.current_stream().cuda_stream if _CUDA else 0
+            if _CUDA:
+                _CURRENT_STREAM = _current_stream_getter(t)
+        return _CURRENT_STREAM() if _CUDA else 0
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream

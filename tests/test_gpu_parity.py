@@ -442,6 +442,30 @@ def test_profile_counts_launches(vg):
     grid.close()
 
 
+def test_default_stream_is_torchs_current_stream(vg):
+    # with no stream given, the binding enqueues on torch's current stream,
+    # also inside a stream context and on a side stream's work order
+    default = torch.cuda.current_stream().cuda_stream
+    assert vg._stream(None) == default
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        assert vg._stream(None) == side.cuda_stream != default
+        w = make("room")
+        g = w.grid
+        grid = vg.Grid(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos)
+        depth = torch.from_numpy(w.frames[0].depth).cuda()
+        out = torch.empty(grid.nvox, dtype=torch.uint8, device="cuda")
+        grid.integrate_depth(depth, w.frames[0].T_wc)
+        grid.read(out)
+    side.synchronize()
+    o = OracleGrid(OracleParams(tuple(g.n), g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, 0),
+                   w.frames[0].robot_pos)
+    o.integrate_depth(w.frames[0].T_wc, w.frames[0].depth)
+    assert_same(out.cpu().numpy().reshape(grid.shape), o.loc, "room frame on a side stream")
+    assert vg._stream(None) == default
+    grid.close()
+
+
 def test_bad_arguments_on_device(vg):
     P = _pair(vg)
     d = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
