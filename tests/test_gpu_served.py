@@ -80,49 +80,54 @@ def test_same_result_alone_and_in_the_mix(vg, plain_max, queue_depth):
     alone, o_alone = _read(s1, cam, target)
     s1.close()
 
-    # in the mix: two client threads interleave all cameras' frames
-    s2 = vg.Server(8 << 30, max_batch=8, queue_depth=queue_depth, pending_frames=24, plain_max=plain_max)
+    # in the mix: four client threads interleave all cameras' frames.  With
+    # one launch at a time frames queue up and share launches whenever they
+    # arrive faster than the server serves them; arrival times depend on the
+    # host, so a run in which no launch happened to hold two frames is
+    # repeated (at most three runs) before that counts as a failure
     ws = [target] + others
-    cams = [_add(s2, w) for w in ws]
-    tickets = []
-    lock = threading.Lock()
+    for attempt in range(3):
+        s2 = vg.Server(8 << 30, max_batch=8, queue_depth=queue_depth, pending_frames=24, plain_max=plain_max)
+        cams = [_add(s2, w) for w in ws]
+        tickets = []
+        lock = threading.Lock()
 
-    def client(idx):
-        local = []
-        rng = np.random.default_rng(idx)
-        pos = {k: 0 for k in idx}
-        while any(pos[k] < len(ws[k].frames) for k in idx):
-            k = rng.choice([k for k in idx if pos[k] < len(ws[k].frames)])
-            f = ws[k].frames[pos[k]]
-            t = s2.submit(cams[k], f.depth, f.T_wc, f.robot_pos, ws[k].cam.scale)
-            if t is None:
-                threading.Event().wait(0.001)
-                continue
-            local.append(t)
-            pos[k] += 1
-        with lock:
-            tickets.extend(local)
+        def client(idx):
+            local = []
+            rng = np.random.default_rng(idx)
+            pos = {k: 0 for k in idx}
+            while any(pos[k] < len(ws[k].frames) for k in idx):
+                k = rng.choice([k for k in idx if pos[k] < len(ws[k].frames)])
+                f = ws[k].frames[pos[k]]
+                t = s2.submit(cams[k], f.depth, f.T_wc, f.robot_pos, ws[k].cam.scale)
+                if t is None:
+                    threading.Event().wait(0.001)
+                    continue
+                local.append(t)
+                pos[k] += 1
+            with lock:
+                tickets.extend(local)
 
-    threads = [threading.Thread(target=client, args=(list(range(0, len(ws), 2)),)),
-               threading.Thread(target=client, args=(list(range(1, len(ws), 2)),))]
-    for th in threads:
-        th.start()
-    for th in threads:
-        th.join()
-    assert all(s2.wait(t) == vg.VG_OK for t in tickets)
-    mixed, o_mixed = _read(s2, cams[0], target)
-    st = s2.stats()
-    assert st["completed"] == st["submitted"] == sum(len(w.frames) for w in ws)
+        threads = [threading.Thread(target=client, args=(list(range(i, len(ws), 4)),)) for i in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        assert all(s2.wait(t) == vg.VG_OK for t in tickets)
+        mixed, o_mixed = _read(s2, cams[0], target)
+        st = s2.stats()
+        assert st["completed"] == st["submitted"] == sum(len(w.frames) for w in ws)
+        for k in range(1, len(ws)):
+            got, o = _read(s2, cams[k], ws[k])
+            want, ow = _plain(vg, ws[k])
+            assert list(o) == list(ow) and np.array_equal(got, want), "camera %d differs from the plain path" % k
+        s2.close()
+        assert list(o_alone) == list(o_mixed)
+        assert np.array_equal(alone, mixed), "%d voxels differ alone vs mixed" % np.count_nonzero(alone != mixed)
+        if queue_depth != 1 or st["mean_batch"] > 1.0:
+            break
     if queue_depth == 1:
         assert st["mean_batch"] > 1.0, st       # frames did share launches
-    for k in range(1, len(ws)):
-        got, o = _read(s2, cams[k], ws[k])
-        want, ow = _plain(vg, ws[k])
-        assert list(o) == list(ow) and np.array_equal(got, want), "camera %d differs from the plain path" % k
-    s2.close()
-
-    assert list(o_alone) == list(o_mixed)
-    assert np.array_equal(alone, mixed), "%d voxels differ alone vs mixed" % np.count_nonzero(alone != mixed)
     want, ow = _plain(vg, target)
     assert list(o_alone) == list(ow) and np.array_equal(alone, want)
 
