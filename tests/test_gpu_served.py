@@ -155,18 +155,28 @@ def test_admission_by_memory_budget(vg):
 
 
 def test_backpressure_and_latency_counters(vg):
-    w = make("robot", robot=60, frames=1)
+    # 1280x720 frames on a 400x400x120 grid take the device longer than a
+    # submit takes, and two threads submit at once, so a 4-frame pool fills
+    w = make("hires", frames=1)
     s = vg.Server(4 << 30, max_batch=4, queue_depth=1, pending_frames=4)
     cam = _add(s, w)
     f = w.frames[0]
-    tickets, busy = [], 0
-    for _ in range(64):
-        t = s.submit(cam, f.depth, f.T_wc, None, w.cam.scale)
-        if t is None:
-            busy += 1
-        else:
-            tickets.append(t)
-    assert busy > 0, "a 4-frame pool never filled"
+    tickets, busy = [], [0, 0]
+
+    def client(i):
+        for _ in range(48):
+            t = s.submit(cam, f.depth, f.T_wc, None, w.cam.scale)
+            if t is None:
+                busy[i] += 1
+            else:
+                tickets.append(t)
+
+    threads = [threading.Thread(target=client, args=(i,)) for i in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert sum(busy) > 0, "a 4-frame pool never filled"
     assert all(s.wait(t) == vg.VG_OK for t in tickets)
     st = s.stats()
     assert st["completed"] == len(tickets) and st["latency_p50_us"] > 0 and st["latency_p99_us"] >= st["latency_p50_us"]
