@@ -1,7 +1,10 @@
 // K2 as its own launch: one CTA per 8-word x 8-row x 8-slice tile of the
-// occupancy plane; the work itself is in vg_units.cuh.  For r = 1, 2, 3 the
+// occupancy plane (4 slices for grids of one to four such tiles per SM);
+// the work itself is in vg_units.cuh.  For r = 1, 2, 3 the
 // radius is a compile-time constant; other radii use a runtime radius.
 #include "vg_units.cuh"
+
+#include <atomic>
 
 namespace vg {
 namespace {
@@ -47,14 +50,17 @@ cudaError_t run_r(const FrameArgs &a, cudaStream_t s, bool short_tiles) {
     }
 }
 
-int g_sms[64];   // SMs per device, read on first use
+std::atomic<int> g_sms[64];   // SMs per device, read on first use (any thread)
 
 int sms_of_current_device() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    if (!g_sms[dev] && cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 0;
-    return g_sms[dev];
+    int n = g_sms[dev].load(std::memory_order_relaxed);
+    if (!n) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        g_sms[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
 }
 
 }  // namespace
