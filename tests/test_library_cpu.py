@@ -176,3 +176,32 @@ def test_batch_and_server_null_handles(vg):
     assert L.vg_server_stats(None, C.byref(st), 0) == vg.VG_EINVAL
     L.vg_batch_destroy(None)
     L.vg_server_destroy(None)
+
+
+def test_current_stream_lookup_falls_back_to_the_public_call(vg):
+    # the binding reads torch's current stream through torch's raw getter
+    # where it exists (the handle of the current device's current stream),
+    # else through torch.cuda.current_stream(); both give the same integer
+    import types
+    calls = []
+
+    class FakeCuda:
+        @staticmethod
+        def current_device():
+            return 3
+
+        @staticmethod
+        def current_stream():
+            calls.append("public")
+            return types.SimpleNamespace(cuda_stream=0xabc)
+
+    with_raw = types.SimpleNamespace(cuda=FakeCuda, _C=types.SimpleNamespace(
+        _cuda_getCurrentRawStream=lambda dev: calls.append(("raw", dev)) or 0xabc))
+    without_raw = types.SimpleNamespace(cuda=FakeCuda, _C=types.SimpleNamespace())
+    assert vg._current_stream_getter(with_raw)() == 0xabc
+    assert calls == [("raw", 3)]
+    assert vg._current_stream_getter(without_raw)() == 0xabc
+    assert calls == [("raw", 3), "public"]
+    # explicit streams pass through unchanged
+    assert vg._stream(0x1234) == 0x1234
+    assert vg._stream(types.SimpleNamespace(cuda_stream=0x99)) == 0x99
