@@ -236,6 +236,20 @@ def test_inflation_radii(vg, r):
     P.close()
 
 
+@pytest.mark.parametrize("n,r", [((200, 200, 100), 1), ((200, 200, 100), 3), ((100, 110, 100), 2)])
+def test_inflate_tile_heights(vg, n, r):
+    # grids with one to four 8-slice inflate tiles per SM take tiles 4 slices
+    # high: 200 x 200 x 100 has 325 tiles 8 words wide, 100 x 110 x 100 has
+    # 182 tiles 4 words wide; every radius and both widths match the oracle
+    rng = np.random.default_rng(sum(n) + r)
+    P = _pair(vg, n=n, vs=0.05, depth=3.0, r=r, pos=(0.01, 0.02, 0.03))
+    for k in range(2):
+        d = rng.uniform(1.5, 3.5, size=(48, 64)).astype(np.float32)
+        d[rng.random(d.shape) < 0.1] = 0
+        P.depth(d, body_pose([0.01, 0.02, 0.03], rng.uniform(-np.pi, np.pi), rng.uniform(-0.3, 0.3)))
+    P.close()
+
+
 @pytest.mark.parametrize("n", [(1, 1, 1), (1, 17, 1), (33, 1, 2), (45, 31, 7), (31, 9, 5), (64, 64, 8),
                                (129, 3, 4), (8500, 3, 2)])
 def test_grid_shapes(vg, n):
