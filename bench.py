@@ -49,10 +49,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle sample budget")
     ap.add_argument("--preroll", type=float, default=1.0, help="seconds of untimed frames before timing")
-    ap.add_argument("--batch-robots", type=int, default=64, help="robots per step of the batched form (0: skip)")
-    ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the batched form")
-    ap.add_argument("--serve-cameras", type=int, default=256, help="cameras of the served form (0: skip)")
-    ap.add_argument("--serve-seconds", type=float, default=5.0, help="seconds of Poisson arrivals")
+    ap.add_argument("--batch-robots", type=int, default=64,
+                    help="robots per step of the batched form, over all ranks (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=200, help="timed steps of the batched form")
+    ap.add_argument("--batch-frames", type=int, default=25,
+                    help="rendered frames per robot of the batched form (cycled over the steps)")
+    ap.add_argument("--serve-cameras", type=int, default=256,
+                    help="cameras of the served form, over all ranks (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="seconds of Poisson arrivals (default 60 on one GPU, 20 per run on several, which "
+                         "all stay held meanwhile)")
     ap.add_argument("--serve-rate", type=float, default=30.0, help="frames per second per camera")
     ap.add_argument("--serve-rate-high", type=float, default=60.0,
                     help="frames per second per camera of a second, heavier served run (0: skip)")
@@ -237,25 +243,32 @@ def workload_config(w, args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def algorithmic_bytes(kind, w, geom):
-    """Bytes one launch of a kernel must move at minimum: its inputs read
-    once and its outputs written once (bit planes of `words` 32-bit words,
-    the 1-byte-per-voxel loc grid, the depth image)."""
-    nvox = w.nvox
-    words = geom["words"]
+def algorithmic_bytes(kind, w):
+    """Bytes one launch of a kernel must move at minimum, as the workload's
+    byte model counts them per voxel: its inputs read once and its outputs
+    written once, with bit planes of N/8 bytes (N = loc voxels), the
+    1-byte-per-voxel loc grid and the depth image.
+      K1 voxelize  depth read + occ_raw written        W*H*bpp + N/8
+      K2 inflate   occ_raw read + occ_inf written      2N/8
+      K3 raytrace  occ_inf read + free, traced written 3N/8
+      K4 merge     loc read + written, 3 planes read   2N + 3N/8
+      K5 shift     loc read + written                  2N"""
+    n = w.nvox
     px = w.cam.W * w.cam.H * (2 if w.cam.dtype == "u16" else 4)
-    return {"voxelize": px + 4 * words,      # depth read, occ_raw plane written
-            "inflate": 8 * words,            # occ_raw read, occ_inf written
-            "raytrace": 12 * words,          # occ_inf read, fr and tr written
-            "merge": 2 * nvox + 12 * words,  # loc read+write, three planes read
-            "shift": 2 * nvox}[kind]
+    return {"voxelize": px + n / 8, "inflate": 2 * n / 8, "raytrace": 3 * n / 8,
+            "merge": 2 * n + 3 * n / 8, "shift": 2 * n, "loc_occupancy": n + n / 8}[kind]
+
+
+def frame_bytes(w):
+    """Algorithmic bytes of one frame (K1..K4, the re-centre inside K4)."""
+    return sum(algorithmic_bytes(k, w) for k in ("voxelize", "inflate", "raytrace", "merge"))
 
 
 # One serial Amanatides-Woo step of the paper's ray trace with its
 # occupancy test and mark: argmin of three tMax (2 compares, 2 selects),
 # loop-end compare, index step, face step, tMax recompute (sub, mul),
 # in-grid test (3 compares), linear index step, bit test (shift, and),
-# mark (or).
+# mark (or).  Reported beside the HBM roofline as an issue-rate model.
 OPS_PER_VISIT = 16
 
 
@@ -313,15 +326,22 @@ def measure_fused_seq(vg, w, args, flush, stream):
             "latency_ms": _pcts(lat), "l2": "flushed before every step"}
 
 
-def measure_batched(vg, args, rank, stream):
+def shard(ids, rank, world):
+    """The units (robots, cameras) rank `rank` of `world` runs: every
+    world-th one, so that the ranks partition the units with no overlap and
+    no collective on the data path."""
+    return [u for u in ids if u % world == rank]
+
+
+def measure_batched(vg, args, dist, stream):
     """The multi-robot workload: every robot's frame of a step in one fused
     launch (eager, and replayed from a CUDA graph), against the plain path
-    on the same frames."""
+    on the same frames.  Robots are sharded over the ranks."""
     import torch
     from synth import make
-    R = args.batch_robots
-    ws = [make("robot", robot=i + 1000 * rank, frames=8) for i in range(R)]
-    F = 8
+    robots = shard(range(args.batch_robots), dist.rank, dist.world)
+    F = args.batch_frames
+    ws = [make("robot", robot=i, frames=F) for i in robots]
     depth = [[torch.from_numpy(f.depth).cuda() for f in w.frames] for w in ws]
     nvox = sum(w.nvox for w in ws)
 
@@ -333,21 +353,26 @@ def measure_batched(vg, args, rank, stream):
         return [(gs[i], depth[i][k % F], w.frames[k % F].T_wc, w.frames[k % F].robot_pos, w.cam.scale)
                 for i, w in enumerate(ws)]
 
+    def agg(vox, secs):
+        return dist.sum(vox) / dist.max(secs) / 1e6
+
     steps = args.batch_steps
-    out = {"workload": "%d robots per step, each its own seeded scene and trajectory; depth %s f32; voxel "
-                       "{0.05, 0.1, 0.2} m; grids 80..256 x 80..256 x 40..96; vox_inf 1-3; %.1f M voxels and "
-                       "%.0f MB of depth per step" % (R, "{320x240, 640x480, 848x480}", nvox / 1e6,
-                                                      sum(w.frames[0].depth.nbytes for w in ws) / 1e6),
+    out = {"workload": "%d robots per step (%d on each of %d GPUs), each its own seeded scene and trajectory "
+                       "(%d rendered frames per robot, cycled); depth %s f32; voxel {0.05, 0.1, 0.2} m; grids "
+                       "80..256 x 80..256 x 40..96; vox_inf 1-3; %.1f M voxels and %.0f MB of depth per step "
+                       "per GPU" % (args.batch_robots, len(robots), dist.world, F, "{320x240, 640x480, 848x480}",
+                                    nvox / 1e6, sum(w.frames[0].depth.nbytes for w in ws) / 1e6),
            "steps": steps, "l2": "inputs and grids (> 1 GB) exceed L2; no flush"}
 
     # batched, eager
     gb = grids()
-    batch = vg.Batch(R)
+    batch = vg.Batch(len(ws))
     ctas, lanes = batch.autotune(frames_of(gb, 0), reps=2, stream=stream)
     for k in range(3):
         batch.step(frames_of(gb, k), stream)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    dist.barrier()
     t0 = time.perf_counter()
     for k in range(steps):
         ev[k][0].record(stream)
@@ -357,9 +382,9 @@ def measure_batched(vg, args, rank, stream):
     wall = time.perf_counter() - t0
     lat = [a.elapsed_time(b) for a, b in ev]
     out["batched"] = {"form": "one persistent fused launch per step", "status": vg.strerror(batch.status()),
-                      "value": nvox * steps / (sum(lat) / 1e3) / 1e6, "unit": "Mvoxel-updates/s",
+                      "value": agg(nvox * steps, sum(lat) / 1e3), "unit": "Mvoxel-updates/s",
                       "step_ms": _pcts(lat), "per_frame_latency_ms": _pcts(lat),
-                      "host_wall_Mvoxel_updates_per_s": nvox * steps / wall / 1e6,
+                      "host_wall_Mvoxel_updates_per_s": agg(nvox * steps, wall),
                       "autotuned": {"ctas_per_sm": ctas, "lanes_per_ray": lanes or "per grid"}}
 
     # batched, replayed from a CUDA graph (prepare on the host, replay)
@@ -372,6 +397,7 @@ def measure_batched(vg, args, rank, stream):
     graph.replay()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    dist.barrier()
     t0 = time.perf_counter()
     for k in range(steps):
         batch.prepare(frames_of(gb, k + 1))
@@ -383,8 +409,8 @@ def measure_batched(vg, args, rank, stream):
     lat = [a.elapsed_time(b) for a, b in ev]
     out["batched_graph"] = {"form": "the fused launch replayed from a CUDA graph",
                             "status": vg.strerror(batch.status()),
-                            "value": nvox * steps / (sum(lat) / 1e3) / 1e6, "unit": "Mvoxel-updates/s",
-                            "step_ms": _pcts(lat), "host_wall_Mvoxel_updates_per_s": nvox * steps / wall / 1e6}
+                            "value": agg(nvox * steps, sum(lat) / 1e3), "unit": "Mvoxel-updates/s",
+                            "step_ms": _pcts(lat), "host_wall_Mvoxel_updates_per_s": agg(nvox * steps, wall)}
     del graph
     batch.close()
     for g in gb:
@@ -400,6 +426,7 @@ def measure_batched(vg, args, rank, stream):
     torch.cuda.synchronize()
     psteps = max(3, steps // 4)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(psteps)]
+    dist.barrier()
     for k in range(psteps):
         ev[k][0].record(stream)
         for i, w in enumerate(ws):
@@ -409,8 +436,9 @@ def measure_batched(vg, args, rank, stream):
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     lat = [a.elapsed_time(b) for a, b in ev]
-    out["plain"] = {"form": "plain: one launch per kernel (K1-K4, the re-centre inside K4), robot after robot", "steps": psteps,
-                    "value": nvox * psteps / (sum(lat) / 1e3) / 1e6, "unit": "Mvoxel-updates/s", "step_ms": _pcts(lat)}
+    out["plain"] = {"form": "plain: one launch per kernel (K1-K4, the re-centre inside K4), robot after robot",
+                    "steps": psteps, "value": agg(nvox * psteps, sum(lat) / 1e3), "unit": "Mvoxel-updates/s",
+                    "step_ms": _pcts(lat)}
     for g in gp:
         g.close()
     out["speedup_batched_vs_plain"] = out["batched"]["value"] / out["plain"]["value"]
@@ -430,55 +458,65 @@ def _arrivals(n_cams, rate, seconds, seed):
         out.append((t, int(rng.integers(n_cams))))
 
 
-def measure_served(vg, args, rank):
+def _lat_pcts(lat_s):
+    ms = np.asarray(lat_s, np.float64) * 1e3
+    return {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)), "max": float(ms.max())}
+
+
+def measure_served(vg, args, dist):
     """Simulated cameras with Poisson arrivals through the continuous-batching
-    server, and through a naive one-frame-at-a-time server for comparison."""
+    server, and through a one-frame-at-a-time queue for comparison.  Both
+    arms measure a frame's latency from its scheduled arrival time to the
+    moment its device work is seen to end, on the host's monotonic clock.
+    Cameras are sharded over the ranks (every rank its own server)."""
     import queue
     import threading
     import torch
     from synth import make
-    nseq = 16
-    seqs = [make("camera", robot=i + 100 * rank, frames=4) for i in range(nseq)]
-    n_req = args.serve_cameras
+    from synth.scenes import CAMERA_KINDS
+    nseq = 2 * CAMERA_KINDS
+    seqs = [make("camera", robot=i, frames=4) for i in range(nseq)]
+    mine = shard(range(args.serve_cameras), dist.rank, dist.world)
     budget = 40 << 30
-    out = {"workload": "%d cameras, Poisson arrivals at %.0f Hz each for %.1f s; depth from {320x240 f32, "
-                       "640x480 f32, 640x480 u16, 1280x720 u16} with grids 80x80x40 at 0.1 m, 200x200x100 at "
-                       "0.05 m or 400x400x120 at 0.05 m (each camera draws one of %d rendered sequences and "
-                       "cycles its 4 frames); %d GB budget" % (n_req, args.serve_rate, args.serve_seconds, nseq,
-                                                               budget >> 30)}
+    out = {"workload": "%d cameras (%d on each of %d GPUs), Poisson arrivals at %.0f Hz each for %.1f s; depth "
+                       "from {320x240 f32/u16, 640x480 f32/u16, 1280x720 u16/f32} with grids 80x80x40 at 0.1 m, "
+                       "200x200x100 at 0.05 m or 400x400x120 at 0.05 m (each camera draws one of %d rendered "
+                       "sequences and cycles its 4 frames); %d GB budget per GPU" % (
+                           args.serve_cameras, len(mine), dist.world, args.serve_rate, args.serve_seconds, nseq,
+                           budget >> 30),
+           "latency": "from each frame's scheduled arrival to the end of its device work (host monotonic clock), "
+                      "in both arms"}
     # ---- continuous batching ---------------------------------------------
     server = vg.Server(budget, max_batch=128, max_width=1280, max_height=720, queue_depth=args.serve_queue_depth,
                        pending_frames=1024, plain_max=args.serve_plain_max)
-    cams = []
-    for i in range(n_req):
-        w = seqs[i % nseq]
+    cams = {}
+    for c in mine:
+        w = seqs[c % nseq]
         g = w.grid
         try:
-            cams.append((server.add_camera(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf,
-                                           w.frames[0].robot_pos), w))
+            cams[c] = (server.add_camera(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf,
+                                         w.frames[0].robot_pos), w)
         except vg.VGError as e:
             if e.status != vg.VG_ENOMEM:
                 raise
             break
-    nc = len(cams)
-    warm = [server.submit(c, w.frames[0].depth, w.frames[0].T_wc, w.frames[0].robot_pos, w.cam.scale)
-            for c, w in cams]
+    warm = [server.submit(cid, w.frames[0].depth, w.frames[0].T_wc, w.frames[0].robot_pos, w.cam.scale)
+            for cid, w in cams.values()]
     for t in warm:
         if t is not None:
             server.wait(t)
     server.stats(reset=True)
-    arr = _arrivals(nc, args.serve_rate, args.serve_seconds, 99 + rank)
+    arr = [(t, c) for t, c in _arrivals(args.serve_cameras, args.serve_rate, args.serve_seconds, 99) if c in cams]
     nclient = 4
     tickets = [[] for _ in range(nclient)]
     late = [0.0] * nclient
-    counter = [1] * nc
+    counter = {c: 1 for c in cams}
 
     # frames of one camera must be submitted in order: give each camera to one client
     per_client = [[] for _ in range(nclient)]
     for t, c in arr:
         per_client[c % nclient].append((t, c))
-    arr = None
-    start = [time.perf_counter()]
+    start = [0.0]
 
     def client_of(k):
         t0 = start[0]
@@ -490,42 +528,51 @@ def measure_served(vg, args, rank):
             cid, w = cams[c]
             f = w.frames[counter[c] % len(w.frames)]
             counter[c] += 1
-            while True:
+            while True:   # a full pool (VG_EBUSY): retry; the latency still counts from t
                 tk = server.submit(cid, f.depth, f.T_wc, f.robot_pos, w.cam.scale)
                 if tk is not None:
-                    tickets[k].append((tk, w.nvox))
+                    tickets[k].append((tk, t0 + t, w.nvox))
                     break
                 time.sleep(0.0002)
 
     threads = [threading.Thread(target=client_of, args=(k,)) for k in range(nclient)]
+    dist.barrier()
     start[0] = time.perf_counter()
     for th in threads:
         th.start()
     for th in threads:
         th.join()
-    ok = all(server.wait(tk) == vg.VG_OK for lst in tickets for tk, _ in lst)
+    ok = all(server.wait(tk) == vg.VG_OK for lst in tickets for tk, _, _ in lst)
     elapsed = time.perf_counter() - start[0]
     st = server.stats()
-    vox = sum(n for lst in tickets for _, n in lst)
+    lat, lat_sub = [], []
+    for lst in tickets:
+        for tk, t_arr, _ in lst:
+            rc, t_sub, t_done = server.ticket_times(tk)
+            if rc == vg.VG_OK:
+                lat.append(t_done - t_arr)
+                lat_sub.append(t_done - t_sub)
+    vox = sum(n for lst in tickets for _, _, n in lst)
+    frames = sum(len(lst) for lst in tickets)
     out["served"] = {"form": "continuous batching: batches of up to 128 frames, %d in flight; a batch of at most "
                              "%s frames runs as per-frame kernel chains on parallel streams, a larger one as one "
                              "fused launch" % (args.serve_queue_depth,
                                                args.serve_plain_max or "4 (the library default)"),
-                     "cameras_admitted": nc, "all_ok": ok, "frames": int(st["completed"]),
-                     "frames_per_s": st["completed"] / elapsed, "value": vox / elapsed / 1e6,
-                     "unit": "Mvoxel-updates/s",
-                     "latency_ms": {"p50": st["latency_p50_us"] / 1e3, "p99": st["latency_p99_us"] / 1e3,
-                                    "max": st["latency_max_us"] / 1e3},
-                     "mean_frames_per_launch": st["mean_batch"], "launches": int(st["batches"]),
+                     "cameras_admitted": int(dist.sum(len(cams))), "all_ok": ok,
+                     "frames": int(dist.sum(frames)), "frames_per_s": dist.sum(frames / elapsed),
+                     "value": dist.sum(vox / elapsed / 1e6), "unit": "Mvoxel-updates/s",
+                     "latency_ms": {k: dist.max(v) for k, v in _lat_pcts(lat).items()},
+                     "latency_from_submit_ms": {k: dist.max(v) for k, v in _lat_pcts(lat_sub).items()},
+                     "mean_frames_per_launch": st["mean_batch"], "launches": int(dist.sum(st["batches"])),
                      "device_bytes_in_use": int(st["bytes_in_use"]),
-                     "client_max_lateness_ms": 1e3 * max(late)}
+                     "client_max_lateness_ms": dist.max(1e3 * max(late))}
     server.close()
 
     # ---- a queue alone: one frame at a time through the plain path ---------
-    grids = []
-    for c, (cid, w) in enumerate(cams):
+    grids = {}
+    for c, (cid, w) in cams.items():
         g = w.grid
-        grids.append(vg.Grid(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos))
+        grids[c] = vg.Grid(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos)
     q = queue.Queue()
     lat = []
     done = [0, 0]
@@ -549,9 +596,9 @@ def measure_served(vg, args, rank):
 
     wt = threading.Thread(target=worker)
     wt.start()
-    arr2 = _arrivals(nc, args.serve_rate, args.serve_seconds, 99 + rank)
+    dist.barrier()
     t0 = time.perf_counter()
-    for t, c in arr2:
+    for t, c in arr:
         now = time.perf_counter() - t0
         if t > now:
             time.sleep(t - now)
@@ -560,14 +607,13 @@ def measure_served(vg, args, rank):
     q.put(None)
     wt.join()
     elapsed = time.perf_counter() - t0
-    for g in grids:
+    for g in grids.values():
         g.close()
-    lat_ms = np.asarray(lat) * 1e3
     out["plain_queue"] = {"form": "a queue alone: one frame at a time, plain path, synchronised per frame",
-                          "frames": done[0], "frames_per_s": done[0] / elapsed, "value": done[1] / elapsed / 1e6,
-                          "unit": "Mvoxel-updates/s", "backlog_when_arrivals_stopped": backlog,
-                          "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
-                                         "p99": float(np.percentile(lat_ms, 99)), "max": float(lat_ms.max())}}
+                          "frames": int(dist.sum(done[0])), "frames_per_s": dist.sum(done[0] / elapsed),
+                          "value": dist.sum(done[1] / elapsed / 1e6), "unit": "Mvoxel-updates/s",
+                          "backlog_when_arrivals_stopped": int(dist.sum(backlog)),
+                          "latency_ms": {k: dist.max(v) for k, v in _lat_pcts(lat).items()}}
     for q in ("p50", "p99"):
         out["speedup_served_vs_plain_queue_%s_latency" % q] = (out["plain_queue"]["latency_ms"][q] /
                                                                max(1e-9, out["served"]["latency_ms"][q]))
@@ -585,6 +631,8 @@ def run_ours(args):
     from paper_2112_13169_gb300 import build as vgbuild
     dist = Dist(args.gpus)
     torch.cuda.set_device(dist.local)
+    if args.serve_seconds is None:
+        args.serve_seconds = 60.0 if dist.world == 1 else 20.0
     vgbuild.build()
     from paper_2112_13169_gb300 import vg
     from synth import make
@@ -690,14 +738,14 @@ def run_ours(args):
     # ---- other forms (reported beside the headline) ------------------------
     forms = {"fused_seq": measure_fused_seq(vg, w, args, flush, stream)}
     if args.batch_robots > 0:
-        forms["multi_robot"] = measure_batched(vg, args, dist.rank, stream)
+        forms["multi_robot"] = measure_batched(vg, args, dist, stream)
     if args.serve_cameras > 0:
-        forms["served"] = measure_served(vg, args, dist.rank)
+        forms["served"] = measure_served(vg, args, dist)
         if args.serve_rate_high > 0:
             # twice the stated load: the one-frame-at-a-time queue falls behind
             hi = argparse.Namespace(**vars(args))
             hi.serve_rate, hi.serve_seconds = args.serve_rate_high, args.serve_seconds_high
-            forms["served_high_load"] = measure_served(vg, hi, dist.rank)
+            forms["served_high_load"] = measure_served(vg, hi, dist)
     t_forms_end = time.time()
 
     if clocks:
@@ -708,36 +756,43 @@ def run_ours(args):
         return 0
 
     hbm_peak, peak_kind, peaks = measured_peaks()
-    geom = {"words": ((g.n[0] + 31) // 32 + 3) // 4 * 4 * g.n[1] * g.n[2]}
     kern = {}
     for name in vg.KERNELS:
         ms, timed, total = prof[name]
         if timed:
             avg_s = ms / timed / 1e3
-            kern[name] = {"avg_us": avg_s * 1e6, "launches": timed, "share": 0.0,
-                          "alg_bytes": algorithmic_bytes(name, w, geom),
-                          "gbs": algorithmic_bytes(name, w, geom) / avg_s / 1e9}
+            alg = algorithmic_bytes(name, w)
+            kern[name] = {"avg_us": avg_s * 1e6, "launches": timed, "share": 0.0, "alg_bytes": alg,
+                          "gbs": alg / avg_s / 1e9}
     tot = sum(v["avg_us"] * v["launches"] for v in kern.values())
     for v in kern.values():
         v["share"] = v["avg_us"] * v["launches"] / tot
     dom = max(kern, key=lambda k: kern[k]["avg_us"] * kern[k]["launches"])
     d = kern[dom]
     visits_per_frame = st["ray_visits"] / max(1, st["frames"])
+    # the dominant kernel against the HBM roofline: its algorithmic bytes per
+    # launch over its average event time, against the measured copy peak
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": d["gbs"] / hbm_peak, "traffic": raytrace_traffic() if dom == "raytrace" else None,
+                "peak_source": "%s hbm_gbs" % peak_kind, "alg_bytes_per_launch": d["alg_bytes"],
+                "avg_us": d["avg_us"]}
     if dom == "raytrace":
-        # issue-bound: ops model of one serial DDA step with its test and mark,
-        # against every lane of every SM issuing once per cycle at max clock
+        # K3 is bound by instruction issue, not bytes: the same launch as
+        # ray-voxel visits x OPS_PER_VISIT lane operations against every lane
+        # of every SM issuing once a cycle at the measured maximum clock
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         mhz = peaks.get("sm_max_mhz", 2070.0)
         peak_tops = sms * 128 * mhz * 1e6 / 1e12
         achieved = visits_per_frame * OPS_PER_VISIT / (d["avg_us"] * 1e-6) / 1e12
-        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                    "frac": achieved / peak_tops, "traffic": raytrace_traffic(),
-                    "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (sms, mhz, peak_kind),
-                    "ops_per_visit": OPS_PER_VISIT, "visits_per_launch": visits_per_frame, "avg_us": d["avg_us"]}
-    else:
-        roofline = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": d["gbs"] / hbm_peak, "traffic": None, "peak_source": peak_kind,
-                    "alg_bytes_per_launch": d["alg_bytes"], "avg_us": d["avg_us"]}
+        roofline["alu_model"] = {"achieved": achieved, "peak": peak_tops, "unit": "T lane-ops/s",
+                                 "frac": achieved / peak_tops, "ops_per_visit": OPS_PER_VISIT,
+                                 "visits_per_launch": visits_per_frame,
+                                 "peak_source": "%d SMs x 128 lanes x %.0f MHz (%s sm_max_mhz)" % (
+                                     sms, mhz, peak_kind)}
+    fb = frame_bytes(w)
+    frame_roofline = {"alg_bytes_per_frame": fb, "ms_per_frame": float(lat_ms.mean()),
+                      "achieved_GBps": fb / (float(lat_ms.mean()) * 1e-3) / 1e9,
+                      "frac": fb / (float(lat_ms.mean()) * 1e-3) / 1e9 / hbm_peak}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -760,8 +815,10 @@ def run_ours(args):
                 "ms_per_step": e2e_s / args.steps * 1e3},
         "gpu_launches": gpu_launches,
         "roofline": roofline,
+        "frame_roofline": frame_roofline,
         "kernels": {k: {"avg_us": round(v["avg_us"], 3), "share": round(v["share"], 4),
-                        "alg_GBps": round(v["gbs"], 1)} for k, v in kern.items()},
+                        "alg_bytes": int(v["alg_bytes"]), "alg_GBps": round(v["gbs"], 1),
+                        "frac_hbm": round(v["gbs"] / hbm_peak, 5)} for k, v in kern.items()},
         "ray_visits_per_frame": visits_per_frame,
         "cpu_baseline": cpu,
         "clocks": {"sm_mhz": summ["sm_mhz"], "sm_max_mhz": summ["sm_max_mhz"], "reasons": summ["reasons"],

@@ -211,7 +211,8 @@ VG_API int vg_read(vg_grid *grid, uint8_t *dst, int32_t dst_mem, int64_t dst_byt
 /*
  * Restore loc_grid and its origin (checkpoint / resume): src holds
  * Nx*Ny*Nz bytes of voxel codes 0..3 (not checked), src_bytes must equal
- * Nx*Ny*Nz.  A pending re-centre is dropped.  Errors: VG_EINVAL, VG_ECUDA.
+ * Nx*Ny*Nz.  A pending re-centre is dropped and the measurement planes are
+ * emptied.  Errors: VG_EINVAL, VG_ECUDA.
  */
 VG_API int vg_write(vg_grid *grid, const uint8_t *src, int32_t src_mem, int64_t src_bytes,
              const int32_t origin[3], void *stream);
@@ -298,9 +299,28 @@ VG_API int vg_batch_status(vg_batch *batch);
  *                             occupancy limit, or 0 for the limit (default).
  *  VG_TUNE_BATCH_LANES        lanes per ray for every frame: 8, 16 or 32, or
  *                             0 to use each grid's own setting (default).
- * Results do not depend on them.  Errors: VG_EINVAL.
+ *  VG_TUNE_BATCH_BARRIER_US   how long a CTA of the fused launch waits at a
+ *                             grid barrier before it gives up, in
+ *                             microseconds, 1 .. 60,000,000, or 0 for the
+ *                             default (4 s).  A step whose wait ran out
+ *                             ends early; vg_batch_status reports
+ *                             VG_ETIMEOUT.
+ *  VG_TUNE_BATCH_BARRIER_EXTRA
+ *                             0 (default) or 1.  With 1 every grid barrier
+ *                             waits for one more arrival than the launch has
+ *                             CTAs, so every wait runs out after the limit
+ *                             above: a fault injection that tests the
+ *                             time-out path without hanging the device.
+ * Results do not depend on the first two.  After VG_ETIMEOUT the step's
+ * grids hold a partial measurement: restore each with vg_write (which also
+ * empties its measurement planes) or destroy it.  Errors: VG_EINVAL.
  */
-enum { VG_TUNE_BATCH_CTAS_PER_SM = 100, VG_TUNE_BATCH_LANES = 101 };
+enum {
+    VG_TUNE_BATCH_CTAS_PER_SM = 100,
+    VG_TUNE_BATCH_LANES = 101,
+    VG_TUNE_BATCH_BARRIER_US = 102,
+    VG_TUNE_BATCH_BARRIER_EXTRA = 103
+};
 VG_API int vg_batch_tune(vg_batch *batch, int32_t knob, int32_t value);
 
 /*
@@ -407,6 +427,16 @@ VG_API int vg_server_submit(vg_server *server, int32_t camera, const void *depth
  * the latencies behind vg_server_stats are kept until a reset). */
 VG_API int vg_server_wait(vg_server *server, uint64_t ticket, int64_t timeout_us);
 
+/* When a request was submitted (the entry of vg_server_submit) and when its
+ * frame's device work was seen to end, in seconds of the host's monotonic
+ * clock (CLOCK_MONOTONIC on Linux, the clock of std::chrono::steady_clock),
+ * so that a caller can measure latency from its own arrival times.  Either
+ * pointer may be NULL.  Returns VG_OK once completed (both written),
+ * VG_ETIMEOUT while pending (only submitted_s written), VG_ECUDA if the
+ * frame failed, VG_EINVAL for an unknown ticket.  Kept for the server's
+ * lifetime (16 bytes per ticket). */
+VG_API int vg_server_ticket_times(vg_server *server, uint64_t ticket, double *submitted_s, double *completed_s);
+
 /* Waits for every queued frame of the camera, then copies its grid to dst
  * (as vg_read) and synchronises.  Errors: VG_EINVAL, VG_ECUDA. */
 VG_API int vg_server_read(vg_server *server, int32_t camera, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes,
@@ -463,10 +493,17 @@ VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
  *  params     grid parameters, as for vg_create (flags are ignored).
  *  origin     the grid's origin (voxel index of voxel (0,0,0) in the world
  *             lattice), e.g. as vg_read reports it; the caller keeps it.
- *  loc        device pointer to the caller's loc_grid, Nx*Ny*Nz bytes in
- *             the layout above, read and updated in place; 16-byte aligned.
- *  depth, width, height, dtype, depth_scale, T_wc, stream
- *             as for vg_integrate_depth, with depth a device pointer.
+ *  loc        the caller's loc_grid in device memory of the current
+ *             device, Nx*Ny*Nz bytes in the layout above, read and updated
+ *             in place; 16-byte aligned.
+ *  depth      W x H pixels as for vg_integrate_depth: device memory of the
+ *             current device, or page-locked host memory, which K1 reads
+ *             in place.
+ *  width, height, dtype, depth_scale, T_wc, stream
+ *             as for vg_integrate_depth.
+ * The kernels run on the current device.  A loc or depth that it cannot
+ * reach (another device's memory, pageable host memory, a pointer CUDA
+ * does not know) is refused with VG_EINVAL before any device work.
  * The four measurement bit planes live in one array of 16 MiB compiled into
  * the library (every GPU that loads the library holds it until the process
  * exits).  A grid whose plane needs more than 2^20 32-bit words

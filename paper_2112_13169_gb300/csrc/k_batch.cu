@@ -17,10 +17,10 @@
 // the same device code as the one-step kernels (vg_units.cuh, vg_rt.cuh).
 // Reads of data an earlier phase wrote skip the L1 (LoadL2).
 //
-// The barrier waits with a clock64 deadline: if the other CTAs do not all
-// arrive within a few seconds, the waiting CTA sets BatchCtl::error and
-// every CTA leaves the kernel, so the host sees VG_ETIMEOUT instead of a
-// hung GPU.  The launch is cooperative, so all CTAs are resident together.
+// The barrier waits with a deadline (BatchCtl::bar_ns, four seconds unless
+// tuned): if the other CTAs do not all arrive in time, the waiting CTA sets
+// BatchCtl::error and every CTA leaves the kernel, so the host sees
+// VG_ETIMEOUT instead of a hung GPU.  The launch is cooperative, so all CTAs are resident together.
 #include "vg_rt.cuh"
 
 namespace vg {
@@ -64,8 +64,17 @@ __device__ __forceinline__ int next_item(const BatchItem *items, int n, int phas
     return i;
 }
 
-// Grid-wide barrier with a deadline.  Returns false (for every thread of
-// the CTA) when the batch has failed.
+__device__ __forceinline__ int64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (int64_t)t;
+}
+
+// Grid-wide barrier with a deadline: the CTAs arrive on a counter, the last
+// of the nblocks + bar_extra arrivals opens the next generation.  A CTA that
+// has waited ctl->bar_ns nanoseconds (or sees the error flag) sets the error
+// flag and gives up.  Returns false (for every thread of the CTA) when the
+// batch has failed.
 __device__ bool grid_sync(BatchCtl *ctl, unsigned nblocks) {
     __shared__ int s_ok;
     __syncthreads();
@@ -74,16 +83,18 @@ __device__ bool grid_sync(BatchCtl *ctl, unsigned nblocks) {
         volatile unsigned *gen = &ctl->bar_gen;
         volatile unsigned *err = &ctl->error;
         const unsigned g = *gen;
+        const unsigned expect = nblocks + ctl->bar_extra;
+        const int64_t limit = ctl->bar_ns;
         __threadfence();
         const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
-        if (arrived == nblocks) {
+        if (arrived == expect) {
             atomicExch(&ctl->bar_count, 0u);
             __threadfence();
             atomicAdd(&ctl->bar_gen, 1u);
         } else {
-            const long long t0 = clock64();
+            const int64_t t0 = global_ns();
             while (*gen == g) {
-                if (*err || clock64() - t0 > kBarrierCycles) {
+                if (*err || global_ns() - t0 > limit) {
                     atomicExch(&ctl->error, 1u);
                     ok = 0;
                     break;

@@ -3,15 +3,11 @@
 // Per-frame host work is argument checking and the set-up arithmetic the
 // paper assigns to the CPU (Sec. IV-B: T^v_c = T^v_w T^w_c is composed on the
 // host and passed to the kernels), plus the pinhole intrinsics and the ray
-// bundle size, all in double and rounded once to float / integer:
-//   origin_k   = floor(p_k / vox_size) - floor(N_k / 2)          (Sec. IV-A)
-//   R^v_c      = R^w_c,  t^v_c = t^w_c - origin * vox_size       (Sec. IV-B)
-//   vox_depth  = lround(depth / vox_size)                         (Sec. IV-C)
-//   hw         = lround(tan(fov_x / 2) * vox_depth), hh likewise
-//   fx         = (W / 2) / tan(fov_x / 2), cx = (W - 1) / 2, y likewise
-// with fov/2 in radians taken as fov_deg * pi / 360.  Everything else runs
-// in the kernels K1..K5, enqueued on the caller's stream without host sync.
+// bundle size, all in double and rounded once to float / integer (the
+// helpers of vg_host.h).  Everything else runs in the kernels K1..K5,
+// enqueued on the caller's stream without host sync.
 #include "vg.h"
+#include "vg_host.h"
 #include "vg_internal.cuh"
 
 #include <cmath>
@@ -61,6 +57,8 @@ struct vg_batch {
     int device;
     int ctas_per_sm;    // 0: occupancy limit
     int lanes;          // 0: each grid's own
+    int64_t bar_ns;     // grid barrier time limit
+    uint32_t bar_extra; // 1: the barrier waits for one CTA too many (tests its time limit)
     uint8_t *dev;       // BatchCtl followed by capacity BatchItems
     uint8_t *host;      // pinned copy
     size_t bytes;       // bytes of the table to copy (set by prepare)
@@ -73,15 +71,10 @@ struct vg_batch {
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
-
-int status_of(cudaError_t e) {
-    if (e == cudaSuccess) return VG_OK;
-    if (e == cudaErrorMemoryAllocation) return VG_ENOMEM;
-    return VG_ECUDA;
-}
-
-double half_fov(float deg) { return (double)deg * kPi / 360.0; }
+using vg::host::bundle_of;
+using vg::host::geom_of;
+using vg::host::origin_of;
+using vg::host::status_of;
 
 bool finite3(const double v[3]) {
     return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
@@ -99,43 +92,10 @@ constexpr uint32_t kLitFlags =
     VG_FLAG_LIT_INFLATE_AFTER_TRACE | VG_FLAG_LIT_SKIP_START_VOXEL | VG_FLAG_LIT_LOC_OCCUPANCY;
 
 bool params_ok(const vg_params *p) {
-    if (!p) return false;
-    int64_t nv = 1;
-    for (int k = 0; k < 3; ++k) {
-        if (p->grid_size[k] < 1) return false;
-        nv *= p->grid_size[k];
-        if (nv >= (int64_t(1) << 31)) return false;
-    }
-    if (!(std::isfinite(p->vox_size) && p->vox_size > 0.0f)) return false;
-    if (!(p->fov_x_deg > 0.0f && p->fov_x_deg < 180.0f)) return false;
-    if (!(p->fov_y_deg > 0.0f && p->fov_y_deg < 180.0f)) return false;
-    if (!(std::isfinite(p->depth) && p->depth > 0.0f)) return false;
-    if (p->vox_inf < 0 || p->vox_inf > vg::kMaxInflate) return false;
-    // K3 indexes plane bits with 32 bits: at most 2^27 plane words (a grid
-    // under 2^31 voxels exceeds that only when Nx is far below 32)
-    {
-        int64_t w = (p->grid_size[0] + 31) / 32, wx = 4;
-        while (wx < w) wx *= 2;
-        if (wx * (int64_t)p->grid_size[1] * p->grid_size[2] >= (int64_t(1) << 27)) return false;
-    }
+    if (!vg::host::shape_ok(p)) return false;
     if (p->flags & ~(VG_FLAG_STATS | kLitFlags)) return false;
     if ((p->flags & VG_FLAG_LIT_INFLATE_AFTER_TRACE) && (p->flags & VG_FLAG_LIT_LOC_OCCUPANCY)) return false;
-    const double vd = (double)p->depth / (double)p->vox_size;
-    if (!(vd < 1.0e6)) return false;
     return true;
-}
-
-PlaneGeom geom_of(const vg_params *p) {
-    PlaneGeom g;
-    g.nx = p->grid_size[0];
-    g.ny = p->grid_size[1];
-    g.nz = p->grid_size[2];
-    const int32_t w = (g.nx + 31) / 32;
-    g.wx = 4;
-    while (g.wx < w) g.wx *= 2;
-    g.words = (int64_t)g.wx * g.ny * g.nz;
-    g.nvox = (int64_t)g.nx * g.ny * g.nz;
-    return g;
 }
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -163,18 +123,6 @@ Layout layout_of(const PlaneGeom &g, uint32_t flags) {
     return L;
 }
 
-void bundle_of(const vg_params *p, int32_t &vd, int32_t &hw, int32_t &hh) {
-    const long d = lround((double)p->depth / (double)p->vox_size);
-    vd = (int32_t)d;
-    hw = (int32_t)lround(tan(half_fov(p->fov_x_deg)) * (double)d);
-    hh = (int32_t)lround(tan(half_fov(p->fov_y_deg)) * (double)d);
-}
-
-void origin_of(const vg_params *p, const double pos[3], int32_t o[3]) {
-    for (int k = 0; k < 3; ++k)
-        o[k] = (int32_t)floor(pos[k] / (double)p->vox_size) - p->grid_size[k] / 2;
-}
-
 // delta = o2 - o1, with an axis whose offset is the grid's size or more
 // (nothing survives the shift) set to the size, so that index sums in the
 // kernels stay small.
@@ -186,25 +134,9 @@ void shift_delta(const vg_params *p, const int32_t o1[3], const int32_t o2[3], i
     }
 }
 
-// Composes T^v_c.  Rejects poses that are not finite, whose rotation block
-// has an entry outside [-1.5, 1.5] (no rotation does), or whose camera lies
-// 2^22 voxels or more from the grid corner: K3's walk length is bounded by
-// the ray's length in voxels, and these limits keep it bounded and keep
-// FP32 voxel coordinates exact to well below one voxel.
+// Composes T^v_c for the grid's current origin (vg::host::pose_vc).
 bool pose_of(const vg_grid *G, const double T_wc[16], vg::Pose32 &T) {
-    if (!T_wc) return false;
-    for (int i = 0; i < 16; ++i)
-        if (!std::isfinite(T_wc[i])) return false;
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) {
-            if (!(std::fabs(T_wc[r * 4 + c]) <= 1.5)) return false;
-            T.R[r * 3 + c] = (float)T_wc[r * 4 + c];
-        }
-        const double t = T_wc[r * 4 + 3] - (double)G->origin[r] * (double)G->p.vox_size;
-        if (!(std::fabs(t / (double)G->p.vox_size) < 4194304.0)) return false;
-        T.t[r] = (float)t;
-    }
-    return true;
+    return vg::host::pose_vc(T_wc, G->origin, G->p.vox_size, T);
 }
 
 // Keeps the caller's current device and switches to the grid's for the call.
@@ -276,16 +208,7 @@ int stage_input(vg_grid *G, const void *src, size_t bytes, cudaStream_t s, const
 }
 
 FrameArgs frame_args(vg_grid *G, const vg::Pose32 &T) {
-    FrameArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.g = G->g;
-    a.T = T;
-    a.vs = G->p.vox_size;
-    a.depth_max = G->p.depth;
-    a.vd = G->vd;
-    a.hw = G->hw;
-    a.hh = G->hh;
-    a.r = G->p.vox_inf;
+    FrameArgs a = vg::host::frame_args(&G->p, G->g, T);
     a.pl = G->pl;
     a.loc = G->loc;
     a.stats = (G->p.flags & VG_FLAG_STATS) ? G->stats : nullptr;
@@ -298,14 +221,7 @@ FrameArgs frame_args(vg_grid *G, const vg::Pose32 &T) {
 FrameArgs depth_frame_args(vg_grid *G, const vg::Pose32 &T, const void *depth, int32_t width, int32_t height,
                            int32_t dtype, float depth_scale) {
     FrameArgs a = frame_args(G, T);
-    a.depth = depth;
-    a.W = width;
-    a.H = height;
-    a.scale = (dtype == VG_DEPTH_U16) ? depth_scale : 1.0f;
-    a.fx = (float)(((double)width / 2.0) / tan(half_fov(G->p.fov_x_deg)));
-    a.fy = (float)(((double)height / 2.0) / tan(half_fov(G->p.fov_y_deg)));
-    a.cx = (float)(((double)width - 1.0) / 2.0);
-    a.cy = (float)(((double)height - 1.0) / 2.0);
+    vg::host::set_depth_frame(a, &G->p, depth, width, height, dtype, depth_scale);
     return a;
 }
 
@@ -612,6 +528,14 @@ int vg_write(vg_grid *G, const uint8_t *src, int32_t src_mem, int64_t src_bytes,
     if (!dg.ok) return VG_ECUDA;
     const cudaMemcpyKind kind = src_mem == VG_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaMemcpyAsync(G->loc, src, (size_t)G->g.nvox, kind, (cudaStream_t)stream);
+    // the measurement planes start empty again (after a failed batch step
+    // they may hold a partial measurement)
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(G->pl.occ_raw, 0, (size_t)G->g.words * 4, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(G->pl.occ_inf, 0, (size_t)G->g.words * 4, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G->pl.fr, 0, (size_t)G->g.words * 4, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G->pl.tr, 0, (size_t)G->g.words * 4, (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
     G->pend_on = false;   // replaced whole
     std::memcpy(G->origin, origin, sizeof(G->origin));
@@ -645,6 +569,7 @@ int vg_batch_create(int32_t capacity, vg_batch **out) {
     vg_batch *B = new (std::nothrow) vg_batch();
     if (!B) return VG_ENOMEM;
     B->capacity = capacity;
+    B->bar_ns = vg::kBarrierNs;
     B->bytes = sizeof(vg::BatchCtl) + (size_t)capacity * sizeof(vg::BatchItem);
     cudaError_t e = cudaGetDevice(&B->device);
     if (e == cudaSuccess) e = configure_device(B->device);
@@ -682,6 +607,16 @@ int vg_batch_tune(vg_batch *B, int32_t knob, int32_t value) {
     if (knob == VG_TUNE_BATCH_LANES) {
         if (value != 0 && value != 8 && value != 16 && value != 32) return VG_EINVAL;
         B->lanes = value;
+        return VG_OK;
+    }
+    if (knob == VG_TUNE_BATCH_BARRIER_US) {
+        if (value < 0 || value > 60000000) return VG_EINVAL;
+        B->bar_ns = value ? (int64_t)value * 1000 : vg::kBarrierNs;
+        return VG_OK;
+    }
+    if (knob == VG_TUNE_BATCH_BARRIER_EXTRA) {
+        if (value != 0 && value != 1) return VG_EINVAL;
+        B->bar_extra = (uint32_t)value;
         return VG_OK;
     }
     return VG_EINVAL;
@@ -806,6 +741,8 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
     }
     std::memset(ctl, 0, sizeof(*ctl));
     ctl->n = n;
+    ctl->bar_ns = B->bar_ns;
+    ctl->bar_extra = B->bar_extra;
     for (int p = 0; p < 4; ++p) ctl->total[p] = total[p];
     B->bytes = sizeof(vg::BatchCtl) + (size_t)n * sizeof(vg::BatchItem);
     B->prepared = true;

@@ -127,13 +127,13 @@ struct BatchCtl {
     unsigned bar_count; // grid barrier: arrivals
     unsigned bar_gen;   // grid barrier: generation
     unsigned error;     // set when a barrier wait ran out
-    unsigned pad1;
+    unsigned bar_extra; // arrivals a barrier waits for beyond the launch's CTAs (0; 1 only to test the time limit)
+    int64_t bar_ns;     // how long a CTA waits at a grid barrier before giving up (globaltimer ns)
 };
 
-// How long a CTA waits at a grid barrier before giving up (clock64 cycles,
-// about four seconds at the GB300's SM clock; a phase of any batch that fits
+// Default of BatchCtl::bar_ns: four seconds (a phase of any batch that fits
 // the device ends far sooner).
-constexpr long long kBarrierCycles = 8000000000LL;
+constexpr int64_t kBarrierNs = 4000000000LL;
 
 inline __host__ __device__ int64_t plane_word(const PlaneGeom &g, int32_t x, int32_t y, int32_t z) {
     return ((int64_t)z * g.ny + y) * g.wx + (x >> 5);

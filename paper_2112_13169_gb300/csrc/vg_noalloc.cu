@@ -18,6 +18,7 @@
 // on its stream before the kernels run.  Calls that overlap on the GPU (on
 // different streams, or from several host threads) race on the array.
 #include "vg.h"
+#include "vg_host.h"
 #include "vg_internal.cuh"
 
 #include <cmath>
@@ -25,8 +26,6 @@
 #include <mutex>
 
 namespace {
-
-constexpr double kPi = 3.14159265358979323846;
 
 // Four planes of up to kPlaneWords 32-bit words each: 16 MiB in total, held
 // by every GPU that loads the library until the process exits.
@@ -52,22 +51,20 @@ cudaError_t setup_device(int dev) {
     return g_setup_err[dev];
 }
 
-double half_fov(float deg) { return (double)deg * kPi / 360.0; }
-
-bool params_ok(const vg_params *p) {
-    if (!p) return false;
-    int64_t nv = 1;
-    for (int k = 0; k < 3; ++k) {
-        if (p->grid_size[k] < 1) return false;
-        nv *= p->grid_size[k];
-        if (nv >= (int64_t(1) << 31)) return false;
+// The address at which the kernels on device `dev` reach p: p itself for
+// device (or managed) memory of that device, the mapped device address for
+// page-locked host memory when host_ok, else NULL (memory of another device,
+// pageable host memory, or a pointer CUDA does not know).  Allocates nothing.
+const void *reachable(const void *p, int dev, bool host_ok) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // not a CUDA-known pointer: clear the error
+        return nullptr;
     }
-    if (!(std::isfinite(p->vox_size) && p->vox_size > 0.0f)) return false;
-    if (!(p->fov_x_deg > 0.0f && p->fov_x_deg < 180.0f)) return false;
-    if (!(p->fov_y_deg > 0.0f && p->fov_y_deg < 180.0f)) return false;
-    if (!(std::isfinite(p->depth) && p->depth > 0.0f)) return false;
-    if (p->vox_inf < 0 || p->vox_inf > vg::kMaxInflate) return false;
-    return (double)p->depth / (double)p->vox_size < 1.0e6;
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+        return at.device == dev ? p : nullptr;
+    if (at.type == cudaMemoryTypeHost && host_ok) return at.devicePointer;
+    return nullptr;
 }
 
 }  // namespace
@@ -76,69 +73,38 @@ extern "C" VG_API int vg_integrate_depth_noalloc(const vg_params *params, const 
                                                  uint8_t *loc, const void *depth, int32_t width,
                                                  int32_t height, int32_t dtype, float depth_scale,
                                                  const double T_wc[16], void *stream) {
-    if (!params_ok(params) || !origin || !loc || !depth || !T_wc) return VG_EINVAL;
-    if (width < 1 || height < 1 || (int64_t)width * height >= (int64_t(1) << 31)) return VG_EINVAL;
-    if (dtype != VG_DEPTH_F32 && dtype != VG_DEPTH_U16) return VG_EINVAL;
-    if (dtype == VG_DEPTH_U16 && !(std::isfinite(depth_scale) && depth_scale > 0.0f)) return VG_EINVAL;
+    if (!vg::host::shape_ok(params) || !origin || !loc || !depth || !T_wc) return VG_EINVAL;
+    if (!vg::host::depth_frame_ok(width, height, dtype, depth_scale)) return VG_EINVAL;
     if (reinterpret_cast<uintptr_t>(loc) % 16 != 0) return VG_EINVAL;
 
     // plane geometry, as for a grid made by vg_create
-    vg::PlaneGeom g;
-    g.nx = params->grid_size[0];
-    g.ny = params->grid_size[1];
-    g.nz = params->grid_size[2];
-    const int32_t w = (g.nx + 31) / 32;
-    g.wx = 4;
-    while (g.wx < w) g.wx *= 2;
-    g.words = (int64_t)g.wx * g.ny * g.nz;
-    g.nvox = (int64_t)g.nx * g.ny * g.nz;
+    const vg::PlaneGeom g = vg::host::geom_of(params);
     if (g.words > kPlaneWords) return VG_ESCRATCH;
 
     // T^v_c from T^w_c and the caller's origin (Sec. IV-B), as vg_integrate_depth does
     vg::Pose32 T;
-    for (int i = 0; i < 16; ++i)
-        if (!std::isfinite(T_wc[i])) return VG_EINVAL;
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) {
-            if (!(std::fabs(T_wc[r * 4 + c]) <= 1.5)) return VG_EINVAL;
-            T.R[r * 3 + c] = (float)T_wc[r * 4 + c];
-        }
-        const double t = T_wc[r * 4 + 3] - (double)origin[r] * (double)params->vox_size;
-        if (!(std::fabs(t / (double)params->vox_size) < 4194304.0)) return VG_EINVAL;
-        T.t[r] = (float)t;
-    }
+    if (!vg::host::pose_vc(T_wc, origin, params->vox_size, T)) return VG_EINVAL;
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = setup_device(dev);
-    if (e != cudaSuccess) return VG_ECUDA;
+    if (e != cudaSuccess) return vg::host::status_of(e);
+    // the kernels run on the current device: loc must be its memory, and
+    // depth its memory or page-locked host memory it reads in place
+    uint8_t *dloc = static_cast<uint8_t *>(const_cast<void *>(reachable(loc, dev, false)));
+    const void *ddepth = reachable(depth, dev, true);
+    if (!dloc || !ddepth) return VG_EINVAL;
+    e = setup_device(dev);
+    if (e != cudaSuccess) return vg::host::status_of(e);
     uint32_t *scratch = g_scratch_dev[dev];
     cudaStream_t s = (cudaStream_t)stream;
 
-    vg::FrameArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.g = g;
-    a.T = T;
-    a.vs = params->vox_size;
-    a.depth_max = params->depth;
-    a.depth = depth;
-    a.W = width;
-    a.H = height;
-    a.scale = (dtype == VG_DEPTH_U16) ? depth_scale : 1.0f;
-    a.fx = (float)(((double)width / 2.0) / tan(half_fov(params->fov_x_deg)));
-    a.fy = (float)(((double)height / 2.0) / tan(half_fov(params->fov_y_deg)));
-    a.cx = (float)(((double)width - 1.0) / 2.0);
-    a.cy = (float)(((double)height - 1.0) / 2.0);
-    const long vd = lround((double)params->depth / (double)params->vox_size);
-    a.vd = (int32_t)vd;
-    a.hw = (int32_t)lround(tan(half_fov(params->fov_x_deg)) * (double)vd);
-    a.hh = (int32_t)lround(tan(half_fov(params->fov_y_deg)) * (double)vd);
-    a.r = params->vox_inf;
+    vg::FrameArgs a = vg::host::frame_args(params, g, T);
+    vg::host::set_depth_frame(a, params, ddepth, width, height, dtype, depth_scale);
     a.pl.occ_raw = scratch;
     a.pl.occ_inf = scratch + g.words;
     a.pl.fr = scratch + 2 * g.words;
     a.pl.tr = scratch + 3 * g.words;
-    a.loc = loc;
+    a.loc = dloc;
     a.stats = nullptr;
 
     // the planes must start empty; the array holds whatever the last call left
@@ -149,5 +115,5 @@ extern "C" VG_API int vg_integrate_depth_noalloc(const vg_params *params, const 
     if (e == cudaSuccess)
         e = vg::launch_raytrace(a, vg::auto_lanes_per_ray(a.vd, a.hw, a.hh), s);
     if (e == cudaSuccess) e = vg::launch_merge(a, s);
-    return e == cudaSuccess ? VG_OK : VG_ECUDA;
+    return vg::host::status_of(e);
 }

@@ -113,6 +113,8 @@ struct vg_server {
     int32_t inflight = 0;
     int64_t fixed_bytes = 0, grid_bytes = 0;
     std::vector<uint8_t> status;   // per ticket: 0 pending, 1 done, 2 failed
+    std::vector<double> t_submit;  // per ticket: submission and completion, monotonic clock seconds
+    std::vector<double> t_done;
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_frames = 0;
     std::vector<float> lat_us;
     std::mutex mu;
@@ -131,9 +133,12 @@ bool can_launch(const vg_server *S) {
 }
 
 // Under the lock: retire a launch all of whose frames have ended.
+double seconds(Clock::time_point t) { return std::chrono::duration<double>(t.time_since_epoch()).count(); }
+
 void finish(vg_server *S, Launch &L) {
     for (const Request &r : L.reqs) {
         S->status[r.ticket] = r.status == VG_OK ? 1 : 2;
+        S->t_done[r.ticket] = seconds(r.done_at);
         if (r.status == VG_OK) {
             ++S->completed;
             S->lat_us.push_back((float)std::chrono::duration<double, std::micro>(r.done_at - r.arrival).count());
@@ -502,6 +507,8 @@ int vg_server_submit(vg_server *S, int32_t camera, const void *depth, int32_t wi
     }
     r.ticket = S->status.size();
     S->status.push_back(0);
+    S->t_submit.push_back(seconds(arrival));
+    S->t_done.push_back(0.0);
     ++S->submitted;
     S->queue.push_back(r);
     if (ticket) *ticket = r.ticket;
@@ -516,6 +523,16 @@ int vg_server_wait(vg_server *S, uint64_t ticket, int64_t timeout_us) {
     auto ready = [&] { return S->status[ticket] != 0; };
     if (timeout_us < 0) S->cv.wait(lk, ready);
     else if (!S->cv.wait_for(lk, std::chrono::microseconds(timeout_us), ready)) return VG_ETIMEOUT;
+    return S->status[ticket] == 1 ? VG_OK : VG_ECUDA;
+}
+
+int vg_server_ticket_times(vg_server *S, uint64_t ticket, double *submitted_s, double *completed_s) {
+    if (!S) return VG_EINVAL;
+    std::lock_guard<std::mutex> g(S->mu);
+    if (ticket >= S->status.size()) return VG_EINVAL;
+    if (submitted_s) *submitted_s = S->t_submit[ticket];
+    if (S->status[ticket] == 0) return VG_ETIMEOUT;
+    if (completed_s) *completed_s = S->t_done[ticket];
     return S->status[ticket] == 1 ? VG_OK : VG_ECUDA;
 }
 

@@ -32,8 +32,8 @@ EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points
            "vg_batch_create", "vg_batch_destroy", "vg_batch_prepare", "vg_batch_enqueue", "vg_batch_step",
            "vg_batch_status", "vg_batch_tune", "vg_batch_autotune", "vg_server_create", "vg_server_destroy",
            "vg_server_add_camera", "vg_server_remove_camera", "vg_server_submit", "vg_server_wait",
-           "vg_server_read", "vg_server_stats")
-VG_TUNE_BATCH_CTAS_PER_SM, VG_TUNE_BATCH_LANES = 100, 101
+           "vg_server_read", "vg_server_stats", "vg_server_ticket_times")
+VG_TUNE_BATCH_CTAS_PER_SM, VG_TUNE_BATCH_LANES, VG_TUNE_BATCH_BARRIER_US, VG_TUNE_BATCH_BARRIER_EXTRA = 100, 101, 102, 103
 KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift", "loc_occupancy")
 VG_TUNE_RT_LANES = 0
 
@@ -119,6 +119,7 @@ def load(path=None):
         "vg_server_wait": (C.c_int, [vp, C.c_uint64, i64]),
         "vg_server_read": (C.c_int, [vp, i32, vp, i32, i64, vp]),
         "vg_server_stats": (C.c_int, [vp, vp, i32]),
+        "vg_server_ticket_times": (C.c_int, [vp, C.c_uint64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -276,8 +277,10 @@ def vg_integrate_depth_noalloc(params, origin, loc, depth, T_wc, depth_scale=1.0
     whose device work overlaps race; see include/vg.h."""
     lptr, lmem, lbytes, ldt = _buffer(loc)
     dptr, dmem, dbytes, dt = _buffer(depth)
-    if lmem != VG_MEM_DEVICE or dmem != VG_MEM_DEVICE:
-        raise ValueError("loc and depth must be device buffers")
+    if lmem != VG_MEM_DEVICE:
+        raise ValueError("loc must be a device buffer")
+    if dmem == VG_MEM_DEVICE and depth.device != loc.device:
+        raise ValueError("loc and depth must be on the same device")
     n = params.grid_size
     if ldt != "uint8" or lbytes != n[0] * n[1] * n[2]:
         raise ValueError("loc must hold Nx*Ny*Nz uint8 voxels")
@@ -285,8 +288,12 @@ def vg_integrate_depth_noalloc(params, origin, loc, depth, T_wc, depth_scale=1.0
     H, W = depth.shape
     o = np.ascontiguousarray(np.asarray(origin, np.int32).reshape(3))
     T, tp = _f64(T_wc, 16)
-    _check(load().vg_integrate_depth_noalloc(C.byref(params), o.ctypes.data, lptr, dptr, int(W), int(H), dtype,
-                                             float(depth_scale), tp, _stream(stream)), "vg_integrate_depth_noalloc")
+    t = _torch()
+    # the library runs on the current device: make it loc's
+    with t.cuda.device(loc.device):
+        _check(load().vg_integrate_depth_noalloc(C.byref(params), o.ctypes.data, lptr, dptr, int(W), int(H),
+                                                 dtype, float(depth_scale), tp, _stream(stream)),
+               "vg_integrate_depth_noalloc")
 
 
 def vg_integrate_points(h, xyz, T_wc, stream=None):
@@ -518,6 +525,16 @@ class Server:
 
     def wait(self, ticket, timeout_us=-1):
         return load().vg_server_wait(self.h, C.c_uint64(ticket), int(timeout_us))
+
+    def ticket_times(self, ticket):
+        """(status, submitted, completed): monotonic-clock seconds, the same
+        clock as time.monotonic() and time.perf_counter() on Linux;
+        completed is None unless the status is VG_OK."""
+        a, b = C.c_double(), C.c_double()
+        rc = load().vg_server_ticket_times(self.h, C.c_uint64(ticket), C.byref(a), C.byref(b))
+        if rc == VG_EINVAL:
+            _check(rc, "vg_server_ticket_times")
+        return rc, a.value, (b.value if rc == VG_OK else None)
 
     def read(self, camera, dst):
         ptr, mem, nbytes, _ = _buffer(dst)

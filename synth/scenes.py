@@ -16,10 +16,11 @@ configurations of the project:
   hires  -- 1280x720 u16 millimetre frames, fov 90x60, depth 6 m, 1000
             primitives, 15% invalid; 400x400x120 at 0.05 m, vox_inf 2
   robot  -- one robot of the batched mix: resolution, voxel size, grid and
-            vox_inf drawn from the stated sets
-  camera -- one camera of the served mix: 320x240 f32, 640x480 f32 or u16,
-            or 1280x720 u16, with a grid of 80x80x40 at 0.1 m, 200x200x100
-            at 0.05 m or 400x400x120 at 0.05 m
+            vox_inf drawn from the stated sets (or given, to pin the mix's
+            extremes)
+  camera -- one camera of the served mix: 320x240 f32 or u16, 640x480 f32
+            or u16, or 1280x720 u16 or f32, with a grid of 80x80x40 at
+            0.1 m, 200x200x100 at 0.05 m or 400x400x120 at 0.05 m
 
 Seeds are recipe_id * 1000 + robot index.  Nothing here computes any step
 of the voxel-grid method; the same frames feed the CPU oracle and the CUDA
@@ -37,6 +38,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
 
 BOX, SPHERE, CYL, ROOM = 0, 1, 2, 3
+
+# kinds of simulated camera in the served mix ("camera"; spec picks one)
+CAMERA_KINDS = 6
 
 # Optical camera (x right, y down, z forward) on a FLU body: columns are the
 # camera axes in body coordinates.
@@ -238,8 +242,12 @@ def _sequence(name, seed, cam, grid, scene_lo, scene_hi, nprims, kinds, nframes,
     return Workload(name, cam, grid, frames, prims)
 
 
-def make(name, frames=None, seed=None, robot=0):
-    """Build a named workload.  frames overrides the frame count."""
+def make(name, frames=None, seed=None, robot=0, spec=None):
+    """Build a named workload.  frames overrides the frame count.  For
+    "robot", spec = (W, H, vox_size, (nx, ny, nz), vox_inf) replaces the
+    drawn resolution, voxel size, grid and radius (the scene and the
+    trajectory are still drawn from the seed); for "camera", spec is the
+    kind of camera, 0 .. CAMERA_KINDS - 1, instead of a drawn one."""
     if name == "room":
         rng = np.random.default_rng(1000 if seed is None else seed)
         cam = Camera(320, 240, 87.0, 58.0)
@@ -276,8 +284,11 @@ def make(name, frames=None, seed=None, robot=0):
         W, H = [(320, 240), (640, 480), (848, 480)][rng.integers(3)]
         vs = float([0.05, 0.1, 0.2][rng.integers(3)])
         n = (int(rng.integers(80, 257)), int(rng.integers(80, 257)), int(rng.integers(40, 97)))
+        r = int(rng.integers(1, 4))
+        if spec is not None:
+            W, H, vs, n, r = spec
         cam = Camera(W, H, 87.0, 58.0)
-        grid = GridSpec(n, vs, 5.0, int(rng.integers(1, 4)))
+        grid = GridSpec(tuple(n), float(vs), 5.0, int(r))
         return _sequence(name, s, cam, grid, [0, 0, 0], [16, 16, 4], 120, [BOX, SPHERE, CYL],
                          frames or 8, 0.05, 0.005)
     if name == "camera":
@@ -285,15 +296,19 @@ def make(name, frames=None, seed=None, robot=0):
         # from the stated set, the grid sized to the camera's range
         s = 5000 + robot if seed is None else seed
         rng = np.random.default_rng(s)
-        kind = int(rng.integers(4))
+        kind = int(rng.integers(CAMERA_KINDS)) if spec is None else int(spec)
         if kind == 0:
             cam, grid = Camera(320, 240, 87.0, 58.0), GridSpec((80, 80, 40), 0.1, 4.0, 1)
         elif kind == 1:
             cam, grid = Camera(640, 480, 87.0, 58.0), GridSpec((200, 200, 100), 0.05, 5.0, 2)
         elif kind == 2:
             cam, grid = Camera(640, 480, 87.0, 58.0, "u16", 0.001), GridSpec((200, 200, 100), 0.05, 5.0, 2)
-        else:
+        elif kind == 3:
             cam, grid = Camera(1280, 720, 90.0, 60.0, "u16", 0.001), GridSpec((400, 400, 120), 0.05, 6.0, 2)
+        elif kind == 4:
+            cam, grid = Camera(320, 240, 87.0, 58.0, "u16", 0.001), GridSpec((80, 80, 40), 0.1, 4.0, 1)
+        else:
+            cam, grid = Camera(1280, 720, 90.0, 60.0), GridSpec((400, 400, 120), 0.05, 6.0, 2)
         return _sequence(name, s, cam, grid, [0, 0, 0], [20, 20, 5], 150, [BOX, SPHERE, CYL], frames or 4,
                          0.08, 0.005)
     raise ValueError("unknown workload " + name)

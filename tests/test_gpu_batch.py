@@ -1,17 +1,25 @@
 """Batched form: many grids' measurements in one persistent fused launch.
 
 Every grid of a batch must equal, voxel for voxel and origin for origin, the
-same grid driven frame by frame through vg_integrate_depth + vg_shift (which
-the parity tests hold equal to the CPU oracle), after every step.
+CPU oracle driven with the same frames (integrate, then re-centre), after
+every step: eager steps, steps replayed from a CUDA graph and steps after
+the autotuner.  The 64-robot mix is the batched configuration as stated:
+depth resolutions from {320x240, 640x480, 848x480}, voxels of 0.05, 0.1 or
+0.2 m, grids from 80x80x40 to 256x256x96 and vox_inf 1-3, with one robot
+pinned at the mix's largest case (848x480, 0.05 m, 256x256x96, vox_inf 3).
 """
 import numpy as np
 import pytest
 
+from gridcheck import assert_grid, oracle_grid
 from synth import make
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+# the batched configuration's largest robot: every extreme of the stated sets
+LARGEST = (848, 480, 0.05, (256, 256, 96), 3)
 
 
 @pytest.fixture(scope="module")
@@ -37,152 +45,187 @@ def _read(grid):
     return out.cpu().numpy(), o
 
 
-def _compare(grids_a, grids_b, what):
-    for k, (ga, gb) in enumerate(zip(grids_a, grids_b)):
-        a, oa = _read(ga)
-        b, ob = _read(gb)
-        assert list(oa) == list(ob), (what, k, oa, ob)
-        bad = np.flatnonzero(a != b)
-        assert bad.size == 0, "%s grid %d: %d voxels differ, first %d: %d vs %d" % (
-            what, k, bad.size, bad[0], a[bad[0]], b[bad[0]])
+def _check(ws, grids, oracles, what):
+    for k, (w, g, og) in enumerate(zip(ws, grids, oracles)):
+        got, o = _read(g)
+        assert_grid(got, o, og, "%s, robot %d (%dx%d, %s m, grid %s, vox_inf %d)" % (
+            what, k, w.cam.W, w.cam.H, w.grid.vox_size, w.grid.n, w.grid.vox_inf))
 
 
-def _workloads():
-    ws = [make("robot", robot=i, frames=3) for i in range(6)]
-    ws.append(make("paper", frames=3))
-    ws.append(make("hires", frames=2))   # u16 depth, 400x400x120 grid
+class Robots:
+    """Workloads, their device frames, the library grids and the oracle
+    grids, stepped together."""
+
+    def __init__(self, vg, ws):
+        self.ws = ws
+        self.depth = [[torch.from_numpy(f.depth).cuda() for f in w.frames] for w in ws]
+        self.grids = [_grid(vg, w) for w in ws]
+        self.oracles = [oracle_grid(w) for w in ws]
+
+    def frames(self, step, recentre=True):
+        out = []
+        for k, (w, g) in enumerate(zip(self.ws, self.grids)):
+            f = w.frames[step]
+            out.append((g, self.depth[k][step], f.T_wc, f.robot_pos if recentre else None, w.cam.scale))
+        return out
+
+    def oracle_step(self, step, recentre=True):
+        for w, og in zip(self.ws, self.oracles):
+            f = w.frames[step]
+            og.integrate_depth(f.T_wc, f.depth, w.cam.scale)
+            if recentre:
+                og.shift(f.robot_pos)
+
+    def check(self, what):
+        _check(self.ws, self.grids, self.oracles, what)
+
+    def close(self):
+        for g in self.grids:
+            g.close()
+
+
+def _mix(n=64, frames=3):
+    ws = [make("robot", robot=i, frames=frames) for i in range(n - 1)]
+    ws.append(make("robot", robot=n - 1, frames=frames, spec=LARGEST))
     return ws
 
 
-def test_batch_equals_plain_frame_by_frame(vg):
-    ws = _workloads()
-    plain = [_grid(vg, w) for w in ws]
-    batched = [_grid(vg, w) for w in ws]
-    batch = vg.Batch(16)
+def test_batched_config_against_the_oracle_eager_and_graph(vg):
+    # the 64-robot mix: steps 0 and 1 eager, steps 2 and 3 replayed from a
+    # CUDA graph captured once; every grid is compared after every step
+    ws = _mix(64, 4)
+    kinds = {(w.cam.W, w.cam.H) for w in ws}
+    assert kinds == {(320, 240), (640, 480), (848, 480)}
+    assert {w.grid.vox_size for w in ws} == {0.05, 0.1, 0.2} and {w.grid.vox_inf for w in ws} == {1, 2, 3}
+    R = Robots(vg, ws)
+    batch = vg.Batch(64)
     try:
-        for step in range(3):
-            frames = []
-            for w, gp, gb in zip(ws, plain, batched):
-                if step >= len(w.frames):
-                    continue
-                f = w.frames[step]
-                d = torch.from_numpy(f.depth).cuda()
-                gp.integrate_depth(d, f.T_wc, w.cam.scale)
-                gp.shift(f.robot_pos)
-                frames.append((gb, d, f.T_wc, f.robot_pos, w.cam.scale))
-            batch.step(frames)
+        for step in range(2):
+            batch.step(R.frames(step))
             assert batch.status() == vg.VG_OK
-            _compare(plain, batched, "step %d" % step)
+            R.oracle_step(step)
+            R.check("eager step %d" % step)
+        batch.prepare(R.frames(2))
+        graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(graph, stream=cap):
+                batch.enqueue(cap)
+        for step in (2, 3):
+            if step > 2:
+                batch.prepare(R.frames(step))
+            graph.replay()
+            torch.cuda.synchronize()
+            assert batch.status() == vg.VG_OK
+            R.oracle_step(step)
+            R.check("graph step %d" % step)
+        del graph
     finally:
         batch.close()
-        for g in plain + batched:
-            g.close()
+        R.close()
+
+
+def test_batch_with_full_size_sequences(vg):
+    # the plain configurations' grids batched together: 640x480 f32 into
+    # 200x200x100 and 1280x720 u16 into 400x400x120, beside two robots
+    ws = [make("seq", frames=3), make("hires", frames=3), make("paper", frames=3),
+          make("robot", robot=5, frames=3)]
+    R = Robots(vg, ws)
+    batch = vg.Batch(8)
+    try:
+        for step in range(3):
+            batch.step(R.frames(step))
+            assert batch.status() == vg.VG_OK
+            R.oracle_step(step)
+            R.check("step %d" % step)
+    finally:
+        batch.close()
+        R.close()
 
 
 def test_batch_without_recentre_and_single_frame(vg):
     w = make("seq", frames=2)
-    gp, gb = _grid(vg, w), _grid(vg, w)
+    R = Robots(vg, [w])
     batch = vg.Batch(1)
-    for f in w.frames:
-        d = torch.from_numpy(f.depth).cuda()
-        gp.integrate_depth(d, f.T_wc)
-        batch.step([(gb, d, f.T_wc, None)])
+    for step in range(2):
+        batch.step(R.frames(step, recentre=False))
         assert batch.status() == vg.VG_OK
-        _compare([gp], [gb], "seq")
+        R.oracle_step(step, recentre=False)
+        R.check("seq step %d" % step)
     batch.close()
-    gp.close()
-    gb.close()
+    R.close()
 
 
 def test_batch_applies_a_pending_shift(vg):
     # a re-centre made with vg_shift before the step, and the step's own
     # re-centre left pending after it, read back both ways
     w = make("robot", robot=7, frames=3)
-    gp, gb = _grid(vg, w), _grid(vg, w)
+    R = Robots(vg, [w])
+    gb, og = R.grids[0], R.oracles[0]
     batch = vg.Batch(2)
     f0, f1, f2 = w.frames
-    for g in (gp, gb):
-        g.shift(f0.robot_pos + np.array([0.3, -0.2, 0.1]))
-    d1, d2 = torch.from_numpy(f1.depth).cuda(), torch.from_numpy(f2.depth).cuda()
-    gp.integrate_depth(d1, f1.T_wc, w.cam.scale)
-    gp.shift(f1.robot_pos)
-    batch.step([(gb, d1, f1.T_wc, f1.robot_pos, w.cam.scale)])
+    p = f0.robot_pos + np.array([0.3, -0.2, 0.1])
+    gb.shift(p)
+    og.shift(p)
+    batch.step(R.frames(1))
     assert batch.status() == vg.VG_OK
-    _compare([gp], [gb], "after the step")              # the read applies the pending re-centre
-    gp.shift(f2.robot_pos)
+    R.oracle_step(1)
+    R.check("after the step")                       # the read applies the pending re-centre
     gb.shift(f2.robot_pos)
-    gp.integrate_depth(d2, f2.T_wc, w.cam.scale)
-    batch.step([(gb, d2, f2.T_wc, None, w.cam.scale)])
+    og.shift(f2.robot_pos)
+    batch.step(R.frames(2, recentre=False))
     assert batch.status() == vg.VG_OK
-    _compare([gp], [gb], "after a step over a vg_shift")
+    R.oracle_step(2, recentre=False)
+    R.check("after a step over a vg_shift")
     batch.close()
-    gp.close()
-    gb.close()
-
-
-def test_batch_replayed_from_a_cuda_graph(vg):
-    ws = [make("robot", robot=i, frames=4) for i in range(10, 14)]
-    plain = [_grid(vg, w) for w in ws]
-    batched = [_grid(vg, w) for w in ws]
-    batch = vg.Batch(8)
-    depth = [[torch.from_numpy(f.depth).cuda() for f in w.frames] for w in ws]
-
-    def frames_of(step):
-        return [(gb, depth[k][step], w.frames[step].T_wc, w.frames[step].robot_pos)
-                for k, (w, gb) in enumerate(zip(ws, batched))]
-
-    # step 0 runs eagerly; it also warms up the launch before capture
-    batch.step(frames_of(0))
-    for k, (w, gp) in enumerate(zip(ws, plain)):
-        gp.integrate_depth(depth[k][0], w.frames[0].T_wc)
-        gp.shift(w.frames[0].robot_pos)
-    torch.cuda.synchronize()
-    batch.prepare(frames_of(1))
-    graph = torch.cuda.CUDAGraph()
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        with torch.cuda.graph(graph, stream=stream):
-            batch.enqueue(stream)
-    # capture does not run the step: replay it, then prepare and replay the rest
-    for step in range(1, 4):
-        if step > 1:
-            batch.prepare(frames_of(step))
-        graph.replay()
-        torch.cuda.synchronize()
-        assert batch.status() == vg.VG_OK
-        for k, (w, gp) in enumerate(zip(ws, plain)):
-            gp.integrate_depth(depth[k][step], w.frames[step].T_wc)
-            gp.shift(w.frames[step].robot_pos)
-        _compare(plain, batched, "graph step %d" % step)
-    del graph
-    batch.close()
-    for g in plain + batched:
-        g.close()
+    R.close()
 
 
 def test_autotune_keeps_results(vg):
     ws = [make("robot", robot=i, frames=2) for i in range(20, 24)]
-    plain = [_grid(vg, w) for w in ws]
-    batched = [_grid(vg, w) for w in ws]
+    R = Robots(vg, ws)
     batch = vg.Batch(4)
-    d0 = [torch.from_numpy(w.frames[0].depth).cuda() for w in ws]
-    frames = [(gb, d0[k], w.frames[0].T_wc, w.frames[0].robot_pos) for k, (w, gb) in enumerate(zip(ws, batched))]
-    ctas, lanes = batch.autotune(frames, reps=2)
+    ctas, lanes = batch.autotune(R.frames(0), reps=2)
     assert ctas >= 1 and lanes in (0, 8, 16, 32)
-    # the autotuner merged frame 0 without re-centring; so does the plain side
-    for k, (w, gp) in enumerate(zip(ws, plain)):
-        gp.integrate_depth(d0[k], w.frames[0].T_wc)
-    _compare(plain, batched, "after autotune")
-    d1 = [torch.from_numpy(w.frames[1].depth).cuda() for w in ws]
-    batch.step([(gb, d1[k], w.frames[1].T_wc, w.frames[1].robot_pos) for k, (w, gb) in enumerate(zip(ws, batched))])
+    # the autotuner merged frame 0 without re-centring; so does the oracle
+    R.oracle_step(0, recentre=False)
+    R.check("after autotune")
+    batch.step(R.frames(1))
     assert batch.status() == vg.VG_OK
-    for k, (w, gp) in enumerate(zip(ws, plain)):
-        gp.integrate_depth(d1[k], w.frames[1].T_wc)
-        gp.shift(w.frames[1].robot_pos)
-    _compare(plain, batched, "after a tuned step")
+    R.oracle_step(1)
+    R.check("after a tuned step")
     batch.close()
-    for g in plain + batched:
-        g.close()
+    R.close()
+
+
+def test_barrier_time_limit_ends_a_step_with_a_timeout(vg):
+    # fault injection on the device's own wait: every grid barrier of the
+    # fused launch waits for one more CTA than the launch has, with a 1 ms
+    # limit, so the first barrier gives up, every CTA leaves the kernel and
+    # the step reports VG_ETIMEOUT; the context stays usable, and a grid
+    # restored with vg_write steps on as the oracle does
+    import time
+    ws = [make("robot", robot=i, frames=2) for i in (2, 3)]
+    R = Robots(vg, ws)
+    batch = vg.Batch(2)
+    batch.tune(vg.VG_TUNE_BATCH_BARRIER_US, 1000)
+    batch.tune(vg.VG_TUNE_BATCH_BARRIER_EXTRA, 1)
+    t0 = time.perf_counter()
+    batch.step(R.frames(0, recentre=False))
+    assert batch.status() == vg.VG_ETIMEOUT
+    assert time.perf_counter() - t0 < 2.0
+    torch.cuda.synchronize()                  # no fault, no hang
+    batch.tune(vg.VG_TUNE_BATCH_BARRIER_EXTRA, 0)
+    for g, og in zip(R.grids, R.oracles):
+        g.write(np.zeros(g.nvox, np.uint8), og.o)
+    batch.step(R.frames(1))
+    assert batch.status() == vg.VG_OK
+    R.oracle_step(1)
+    R.check("after a timed-out step and vg_write")
+    with pytest.raises(vg.VGError):
+        batch.tune(vg.VG_TUNE_BATCH_BARRIER_EXTRA, 2)
+    batch.close()
+    R.close()
 
 
 def test_batch_rejects_bad_frames(vg):

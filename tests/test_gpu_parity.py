@@ -7,6 +7,7 @@ voxel, both states and the count; none is tolerated.
 import numpy as np
 import pytest
 
+from gridcheck import assert_same
 from oracle import OracleGrid, OracleParams
 from oracle.oracle import LIT_INFLATE_AFTER_TRACE, LIT_LOC_OCCUPANCY, LIT_SKIP_START
 from synth import body_pose, make
@@ -25,19 +26,6 @@ def vg():
     from paper_2112_13169_gb300 import vg as vgmod
     vgmod.load()
     return vgmod
-
-
-def assert_same(got, ref, what):
-    bad = np.argwhere(got != ref)
-    if len(bad):
-        z, y, x = bad[0]
-        pairs = {}
-        for b in bad[:100000]:
-            k = (int(got[tuple(b)]), int(ref[tuple(b)]))
-            pairs[k] = pairs.get(k, 0) + 1
-        raise AssertionError("%s: %d voxels differ; first (x=%d, y=%d, z=%d) gpu=%d oracle=%d; "
-                             "(gpu, oracle) pair counts %s" % (what, len(bad), x, y, z, got[z, y, x],
-                                                               ref[z, y, x], pairs))
 
 
 class Pair:
@@ -122,17 +110,21 @@ def test_room_single_frame(vg):
 
 
 def test_paper_shapes_sequence(vg):
-    run_workload(vg, make("paper", frames=6), 6)
+    # the paper's standard set-up, all 100 frames
+    run_workload(vg, make("paper"), 100)
 
 
 def test_sequence_full_size(vg):
-    # 640x480 f32, 200x200x100 grid at 0.05 m, vox_inf 2, shift every frame,
-    # in the launch configuration the benchmark times
-    run_workload(vg, make("seq", frames=4), 4)
+    # the whole plain sequence: 100 frames of 640x480 f32 into a 200x200x100
+    # grid at 0.05 m, vox_inf 2, re-centred after every frame, in the launch
+    # configuration the benchmark times; compared after every frame
+    run_workload(vg, make("seq"), 100)
 
 
 def test_hires_u16_full_size(vg):
-    run_workload(vg, make("hires", frames=2), 2)
+    # the whole high-resolution sequence: 50 frames of 1280x720 u16 into a
+    # 400x400x120 grid
+    run_workload(vg, make("hires"), 50)
 
 
 @pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8, 16, 32])

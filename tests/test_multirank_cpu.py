@@ -3,9 +3,11 @@
 With N GPUs the benchmark runs one process per GPU: every rank integrates
 its own robot's sequence (the path shards by robot and has no collective
 on the data path), and only the barrier and the max / sum of the timings
-cross ranks.  These tests run that plumbing as two gloo ranks on the CPU:
-the reductions, that every rank gets its own robot, and that the reference
-arm under torchrun prints one line from rank 0 while rank 1 exits cleanly.
+cross ranks.  The batched and served forms shard their robots and cameras
+over the ranks the same way.  These tests run that plumbing as two gloo
+ranks on the CPU: the reductions, that every rank gets its own robot, that
+the ranks partition the robots and cameras, and that the reference arm
+under torchrun prints one line from rank 0 while rank 1 exits cleanly.
 """
 import json
 import os
@@ -41,9 +43,13 @@ def _rank_main(rank, world, port, out):
     total = d.sum(10.0 * (rank + 1))
     w = make("seq", frames=1, seed=bench.rank_seed(rank))
     first_depth = float(w.frames[0].depth[::37, ::41].sum())
+    # the batched and served forms: this rank's robots and cameras
+    robots = bench.shard(range(64), rank, world)
+    cams = bench.shard(range(256), rank, world)
+    n_all = d.sum(len(robots)) + 1000 * d.sum(len(cams))
     d.barrier()
     d.close()
-    out.put((rank, slowest, total, bench.rank_seed(rank), first_depth))
+    out.put((rank, slowest, total, bench.rank_seed(rank), first_depth, robots, cams, n_all))
 
 
 @pytest.mark.timeout(300)
@@ -59,9 +65,15 @@ def test_two_gloo_ranks_reduce_timings_and_run_independent_robots():
         p.join(240)
         assert p.exitcode == 0, "rank process failed"
     res = sorted(out.get() for _ in range(world))
-    for rank, slowest, total, _, _ in res:
+    for rank, slowest, total, _, _, _, _, n_all in res:
         assert slowest == 2.5          # max over ranks of 1.5 + rank
         assert total == 30.0           # sum over ranks of 10 * (rank + 1)
+        assert n_all == 64 + 1000 * 256
+    # the ranks partition the 64 robots and the 256 cameras: no unit twice, none left out
+    for k, n in ((5, 64), (6, 256)):
+        units = [u for r in res for u in r[k]]
+        assert sorted(units) == list(range(n))
+        assert all(len(r[k]) == n // world for r in res)
     seeds = [r[3] for r in res]
     assert len(set(seeds)) == world    # every rank its own robot
     assert res[0][4] != res[1][4]      # ... and so its own depth frames
