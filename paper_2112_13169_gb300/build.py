@@ -51,7 +51,8 @@ def build(force=False, verbose=False):
     """Compile and link libvg.so if any source changed; return its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, h) for h in ("vg_internal.cuh", "vg_units.cuh", "vg_rt.cuh")]
+    headers = [os.path.join(CSRC, h) for h in ("vg_internal.cuh", "vg_units.cuh", "vg_rt.cuh", "vg_sync.cuh",
+                                               "vg_host.h")]
     headers.append(os.path.join(ROOT, "include", "vg.h"))
     objs, jobs = [], []
     for src in SOURCES:

@@ -22,6 +22,7 @@
 // BatchCtl::error and every CTA leaves the kernel, so the host sees
 // VG_ETIMEOUT instead of a hung GPU.  The launch is cooperative, so all CTAs are resident together.
 #include "vg_rt.cuh"
+#include "vg_sync.cuh"
 
 namespace vg {
 namespace {
@@ -62,52 +63,6 @@ __device__ __forceinline__ int64_t run_begin(int64_t total, unsigned b, unsigned
 __device__ __forceinline__ int next_item(const BatchItem *items, int n, int phase, int64_t u, int i) {
     while (i + 1 < n && __ldg(&items[i + 1].off[phase]) <= u) ++i;
     return i;
-}
-
-__device__ __forceinline__ int64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return (int64_t)t;
-}
-
-// Grid-wide barrier with a deadline: the CTAs arrive on a counter, the last
-// of the nblocks + bar_extra arrivals opens the next generation.  A CTA that
-// has waited ctl->bar_ns nanoseconds (or sees the error flag) sets the error
-// flag and gives up.  Returns false (for every thread of the CTA) when the
-// batch has failed.
-__device__ bool grid_sync(BatchCtl *ctl, unsigned nblocks) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned *gen = &ctl->bar_gen;
-        volatile unsigned *err = &ctl->error;
-        const unsigned g = *gen;
-        const unsigned expect = nblocks + ctl->bar_extra;
-        const int64_t limit = ctl->bar_ns;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
-        if (arrived == expect) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            const int64_t t0 = global_ns();
-            while (*gen == g) {
-                if (*err || global_ns() - t0 > limit) {
-                    atomicExch(&ctl->error, 1u);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-        if (*err) ok = 0;
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
 }
 
 template <int LPR>
