@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=100, help="frames in the synthetic sequence")
     ap.add_argument("--lanes", type=int, default=0, help="K3 lanes per ray (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the library's default schedule (no autotuner)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle sample budget")
     ap.add_argument("--preroll", type=float, default=1.0, help="seconds of untimed frames before timing")
     ap.add_argument("--batch-robots", type=int, default=64,
@@ -367,7 +368,7 @@ def measure_batched(vg, args, dist, stream):
     # batched, eager
     gb = grids()
     batch = vg.Batch(len(ws))
-    ctas, lanes = batch.autotune(frames_of(gb, 0), reps=2, stream=stream)
+    tuned = batch.autotune(frames_of(gb, 0), reps=2, stream=stream)
     for k in range(3):
         batch.step(frames_of(gb, k), stream)
     torch.cuda.synchronize()
@@ -385,7 +386,7 @@ def measure_batched(vg, args, dist, stream):
                       "value": agg(nvox * steps, sum(lat) / 1e3), "unit": "Mvoxel-updates/s",
                       "step_ms": _pcts(lat), "per_frame_latency_ms": _pcts(lat),
                       "host_wall_Mvoxel_updates_per_s": agg(nvox * steps, wall),
-                      "autotuned": {"ctas_per_sm": ctas, "lanes_per_ray": lanes or "per grid"}}
+                      "autotuned": dict(tuned, lanes=tuned["lanes"] or "per grid")}
 
     # batched, replayed from a CUDA graph (prepare on the host, replay)
     batch.prepare(frames_of(gb, 0))
@@ -649,8 +650,13 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     out_host = torch.empty(w.nvox, dtype=torch.uint8).pin_memory()
 
-    def new_grid(flags=0):
+    sched = {}   # the schedule the autotuner picks (knob -> value); empty: the library's defaults
+
+    def new_grid(flags=0, tuned=True):
         gr = vg.Grid(g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, poss[0], flags=flags)
+        if tuned:
+            for knob, value in sched.items():
+                gr.set(knob, value)
         if args.lanes:
             gr.tune(args.lanes)
         return gr
@@ -677,6 +683,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     grid.close()
 
+    # the per-grid autotuner picks the schedule on the sequence's first frame
+    # (untimed); the timed region runs with it, and the library's default
+    # schedule is timed beside it over the same steps
+    tune_info = None
+    if not args.no_tune:
+        grid = new_grid(tuned=False)
+        best = grid.autotune(depth_dev[0], Ts[0], scale, reps=15)
+        grid.close()
+        tiles = {v: k for k, v in vg.TILE_NAMES.items()}
+        sched.update({vg.VG_TUNE_INFLATE_TILE: tiles[best["tile"]], vg.VG_TUNE_RT_LANES: best["lanes"],
+                      vg.VG_TUNE_RT_CTAS_PER_SM: best["ctas_per_sm"], vg.VG_TUNE_MERGE_WORDS: best["merge_words"]})
+        tune_info = {"schedule": best}
+
     # ---- timed region: per-frame device time ------------------------------
     grid = new_grid()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -696,6 +715,23 @@ def run_ours(args):
     launches1 = grid.profile_read()
     gpu_launches = int(sum(launches1[k][2] - launches0[k][2] for k in vg.KERNELS))
     grid.close()
+
+    if tune_info is not None:
+        # the same steps with the library's default schedule
+        grid = new_grid(tuned=False)
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            ev2[k][0].record(stream)
+            step(grid, k)
+            ev2[k][1].record(stream)
+        torch.cuda.synchronize()
+        grid.close()
+        lat0 = np.array([a.elapsed_time(b) for a, b in ev2])
+        tune_info["default_schedule_latency_ms"] = {"p50": float(np.percentile(lat0, 50)),
+                                                    "p99": float(np.percentile(lat0, 99)),
+                                                    "mean": float(lat0.mean())}
+        tune_info["gain_mean"] = float(lat0.mean() / lat_ms.mean())
 
     total_s = float(lat_ms.sum()) / 1e3
     total_s_max = dist.max(total_s)
@@ -820,6 +856,7 @@ def run_ours(args):
                         "alg_bytes": int(v["alg_bytes"]), "alg_GBps": round(v["gbs"], 1),
                         "frac_hbm": round(v["gbs"] / hbm_peak, 5)} for k, v in kern.items()},
         "ray_visits_per_frame": visits_per_frame,
+        "autotune": tune_info,
         "cpu_baseline": cpu,
         "clocks": {"sm_mhz": summ["sm_mhz"], "sm_max_mhz": summ["sm_max_mhz"], "reasons": summ["reasons"],
                    "samples": summ["samples"]},

@@ -145,7 +145,9 @@ typedef struct {
 VG_API int vg_create(const vg_params *params, const double robot_pos_w[3], void *stream,
               vg_grid **out);
 
-/* Frees the grid (synchronises the device first).  NULL is accepted. */
+/* Frees the grid (synchronises the device first).  NULL is accepted.  The
+ * paper has no counterpart (its grids live for the whole run); this is the
+ * library's resource convention. */
 VG_API void vg_destroy(vg_grid *grid);
 
 /*
@@ -194,6 +196,9 @@ VG_API int vg_integrate_points(vg_grid *grid, const float *xyz, int32_t mem, int
 VG_API int vg_shift(vg_grid *grid, const double robot_pos_w[3], void *stream);
 
 /*
+ * The paper has no counterpart: its planner reads loc_grid in place (Sec.
+ * IV, Fig. 1); a library whose grids live on the device hands them out with
+ * a copy.
  * Copy loc_grid (Nx*Ny*Nz bytes, layout above) to dst, enqueued on stream;
  * dst is valid once that work completes.  dst_mem is VG_MEM_DEVICE or
  * VG_MEM_HOST; dst_bytes must be >= Nx*Ny*Nz.  origin (may be NULL)
@@ -209,6 +214,8 @@ VG_API int vg_read(vg_grid *grid, uint8_t *dst, int32_t dst_mem, int64_t dst_byt
             int32_t origin[3], void *stream);
 
 /*
+ * The paper has no counterpart (no checkpointing); this is the library's
+ * resume path, and the way to restore a grid after a failed batch step.
  * Restore loc_grid and its origin (checkpoint / resume): src holds
  * Nx*Ny*Nz bytes of voxel codes 0..3 (not checked), src_bytes must equal
  * Nx*Ny*Nz.  A pending re-centre is dropped and the measurement planes are
@@ -217,7 +224,8 @@ VG_API int vg_read(vg_grid *grid, uint8_t *dst, int32_t dst_mem, int64_t dst_byt
 VG_API int vg_write(vg_grid *grid, const uint8_t *src, int32_t src_mem, int64_t src_bytes,
              const int32_t origin[3], void *stream);
 
-/* Current origin (host-side state; no device work). */
+/* Current origin (host-side state; no device work): the voxel index of
+ * voxel (0,0,0) in the world lattice, as Sec. IV-A places it. */
 VG_API int vg_get_origin(const vg_grid *grid, int32_t origin[3]);
 
 /* Device bytes one grid with these parameters holds (0 if invalid). */
@@ -299,6 +307,16 @@ VG_API int vg_batch_status(vg_batch *batch);
  *                             occupancy limit, or 0 for the limit (default).
  *  VG_TUNE_BATCH_LANES        lanes per ray for every frame: 8, 16 or 32, or
  *                             0 to use each grid's own setting (default).
+ *  VG_TUNE_BATCH_INFLATE_SLICES
+ *                             slices of an inflate tile (phase 2): 8 (the
+ *                             default; 0 selects it) or 4.
+ *  VG_TUNE_BATCH_MERGE_WORDS  plane words per merge unit (phase 4) of a
+ *                             grid whose merge applies a re-centre: 512 (the
+ *                             default; 0 selects it) or 256.
+ *  VG_TUNE_BATCH_SPREAD       1 (default): each frame's rays are spread over
+ *                             proportionally more phase-3 units, so that the
+ *                             CTAs' contiguous runs of units come out even;
+ *                             0: one unit per group of 256 / LPR rays.
  *  VG_TUNE_BATCH_BARRIER_US   how long a CTA of the fused launch waits at a
  *                             grid barrier before it gives up, in
  *                             microseconds, 1 .. 60,000,000, or 0 for the
@@ -311,7 +329,7 @@ VG_API int vg_batch_status(vg_batch *batch);
  *                             CTAs, so every wait runs out after the limit
  *                             above: a fault injection that tests the
  *                             time-out path without hanging the device.
- * Results do not depend on the first two.  After VG_ETIMEOUT the step's
+ * Results do not depend on any knob but the last.  After VG_ETIMEOUT the step's
  * grids hold a partial measurement: restore each with vg_write (which also
  * empties its measurement planes) or destroy it.  Errors: VG_EINVAL.
  */
@@ -319,20 +337,27 @@ enum {
     VG_TUNE_BATCH_CTAS_PER_SM = 100,
     VG_TUNE_BATCH_LANES = 101,
     VG_TUNE_BATCH_BARRIER_US = 102,
-    VG_TUNE_BATCH_BARRIER_EXTRA = 103
+    VG_TUNE_BATCH_BARRIER_EXTRA = 103,
+    VG_TUNE_BATCH_INFLATE_SLICES = 104,
+    VG_TUNE_BATCH_MERGE_WORDS = 105,
+    VG_TUNE_BATCH_SPREAD = 106
 };
 VG_API int vg_batch_tune(vg_batch *batch, int32_t knob, int32_t value);
 
 /*
- * Autotuner: times `reps` steps of the given frames for every candidate
- * setting of the knobs above (re-centring switched off, so every timed step
- * merges the same measurements into the grids, which leaves them as one
- * step would), keeps the fastest setting in the batch and writes it to
- * best[2] = {ctas_per_sm, lanes} (may be NULL).  Synchronises the device.
- * Errors: as vg_batch_step, VG_ETIMEOUT.
+ * Autotuner of the batch's schedule: times `reps` steps of the given frames
+ * (re-centring switched off, so every timed step merges the same
+ * measurements into the grids, which leaves them as one step would) for
+ * each candidate value of one schedule knob at a time -- CTAs per SM (1 ..
+ * the occupancy limit), lanes per ray (per grid, 8, 16, 32), inflate tile
+ * slices (8, 4), merge words per unit (512, 256), phase-3 spread (on, off)
+ * -- with the other knobs at the best values found so far (coordinate
+ * descent), keeps the fastest setting in the batch and writes it to best[5]
+ * = {ctas_per_sm, lanes, inflate_slices, merge_words, spread} (may be NULL).
+ * Synchronises the device.  Errors: as vg_batch_step, VG_ETIMEOUT.
  */
 VG_API int vg_batch_autotune(vg_batch *batch, const vg_frame *frames, int32_t n, int32_t reps,
-                             void *stream, int32_t best[2]);
+                             void *stream, int32_t best[5]);
 
 /*
  * Served form: a request loop for many cameras with continuous batching.
@@ -476,10 +501,52 @@ VG_API int vg_profile_read(vg_grid *grid, double ms[VG_NKERNELS], int64_t timed[
  *                    16 or 32, or 0 for automatic (the default: the fewest
  *                    lanes, at least 8, whose share of the longest ray fits
  *                    the per-lane visit buffer).  Results do not depend on it.
- * Errors: VG_EINVAL.
+ *  VG_TUNE_INFLATE_TILE
+ *                    K2's tile of plane words: VG_TILE_AUTO (the default:
+ *                    8 words x 8 rows x 8 slices, 4 slices when the grid has
+ *                    one to four 8-slice tiles per SM, 4 words for rows of 4
+ *                    words), or VG_TILE_4x8x4, _4x8x8, _8x8x4, _8x8x8
+ *                    (words x rows x slices; 8-word tiles fall back to 4 on
+ *                    rows of 4 words).
+ *  VG_TUNE_RT_CTAS_PER_SM
+ *                    K3's CTAs per SM, 1 .. the occupancy limit (5), or 0
+ *                    for the limit (default).
+ *  VG_TUNE_MERGE_WORDS
+ *                    plane words per CTA of K4 when it applies a pending
+ *                    re-centre: 256 (default) or 512.
+ * Results do not depend on any of them.  Errors: VG_EINVAL.
  */
-enum { VG_TUNE_RT_LANES = 0 };
+enum {
+    VG_TUNE_RT_LANES = 0,
+    VG_TUNE_INFLATE_TILE = 1,
+    VG_TUNE_RT_CTAS_PER_SM = 2,
+    VG_TUNE_MERGE_WORDS = 3
+};
+enum { VG_TILE_AUTO = 0, VG_TILE_4x8x4 = 1, VG_TILE_4x8x8 = 2, VG_TILE_8x8x4 = 3, VG_TILE_8x8x8 = 4 };
 VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
+
+/*
+ * Autotuner of the per-frame kernels' schedule.  Measures the median CUDA
+ * event time of `reps` (1 .. 1000) measurements of the given depth frame
+ * (arguments as for vg_integrate_depth), each starting with a cold L2 (a
+ * write of twice the L2's size to a scratch buffer the call allocates and
+ * frees), first under the grid's schedule as it stands, then for each
+ * candidate value of one knob at a time -- K2's tile (the four shapes),
+ * K3's lanes per ray (8, 16, 32), K3's CTAs per SM (1..5) and K4's words
+ * per CTA (256, 512) -- with the other knobs at the best values found so
+ * far; a candidate wins only if it is at least 2 % faster.  Keeps the
+ * winning schedule in the grid and writes it to best[4] = {tile, lanes,
+ * ctas_per_sm, merge_words} (tile VG_TILE_AUTO and ctas_per_sm 0 where the
+ * defaults won; may be NULL).  Each timed measurement merges the frame over
+ * a re-centre by zero, so K4 runs the re-centring merge that a moving
+ * robot's frames take; merging the same measurement again leaves the grid
+ * as one merge leaves it.  A re-centre pending at the call is applied
+ * first.  Synchronises the stream.
+ * Errors: as vg_integrate_depth; VG_ENOMEM for the scratch buffer.
+ */
+VG_API int vg_autotune(vg_grid *grid, const void *depth, int32_t mem, int32_t width, int32_t height,
+                       int32_t dtype, float depth_scale, const double T_wc[16], int32_t reps, void *stream,
+                       int32_t best[4]);
 
 /*
  * One measurement without any device allocation.  The paper has no
@@ -524,7 +591,8 @@ VG_API int vg_integrate_depth_noalloc(const vg_params *params, const int32_t ori
                                       int32_t height, int32_t dtype, float depth_scale,
                                       const double T_wc[16], void *stream);
 
-/* Static description of a status code. */
+/* Static description of a status code (a library convention; the paper
+ * defines no error handling). */
 VG_API const char *vg_strerror(int status);
 
 #ifdef __cplusplus

@@ -3,11 +3,12 @@
 // One cooperative launch of k_batch runs, for every frame of a batch (each
 // with its own grid, resolution, voxel size and radius), the whole path:
 //   phase 1  K1 voxelize           units of 1024 pixels
-//   phase 2  K2 inflate            8 x 8 x 8-word tiles (radius 1..3)
+//   phase 2  K2 inflate            8 (or 4) words x 8 rows x 8 (or 4)
+//                                  slices (radius 1..3)
 //   phase 3  K3 ray trace          groups of at most 256 / LPR rays (a
 //                                  frame's rays spread over its units)
-//   phase 4  K4 merge              256 plane words (512 with a pending
-//                                  re-centre)
+//   phase 4  K4 merge              256 plane words (512, or 256 if tuned,
+//                                  with a pending re-centre)
 // with a grid-wide barrier between phases.  A frame's re-centre (K5) is not
 // a phase: it is left pending on its grid and applied by that grid's next
 // merge, which then writes the whole grid out of place (merge_shift_unit).
@@ -72,6 +73,17 @@ __device__ __forceinline__ unsigned group_lpr(const FrameArgs &a, int buffered, 
     return rt_group<LPR, units::LoadL2>(a, S, b, grp, G, buffered, box_fr, box_tr, occ_box, buf);
 }
 
+// One inflate tile of TXW words x 8 rows x TZ slices of a batch frame.
+template <int TXW, int TZ>
+__device__ __forceinline__ void inflate_unit(const BatchItem &it, int tx, int ty, int tz, uint32_t *sm) {
+    const PlaneGeom &g = it.a.g;
+    switch (it.a.r) {
+    case 1: units::inflate_tile<1, TXW, 8, TZ, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, sm); break;
+    case 2: units::inflate_tile<2, TXW, 8, TZ, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, sm); break;
+    default: units::inflate_tile<3, TXW, 8, TZ, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, sm); break;
+    }
+}
+
 // Copies a frame's arguments into shared memory, by the threads of the CTA
 // (the caller places the barriers).
 __device__ __forceinline__ void stage_args(const FrameArgs &src, FrameArgs &dst) {
@@ -132,19 +144,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
             const int tx = (int)(local - t01 * t0);
             const int ty = (int)(t01 % (uint32_t)it.tiles[1]);
             const int tz = (int)(t01 / (uint32_t)it.tiles[1]);
-            const PlaneGeom &g = it.a.g;
-            if (it.txw == 8) {
-                switch (it.a.r) {
-                case 1: units::inflate_tile<1, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
-                case 2: units::inflate_tile<2, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
-                default: units::inflate_tile<3, 8, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
-                }
-            } else {
-                switch (it.a.r) {
-                case 1: units::inflate_tile<1, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 1, tx, ty, tz, dyn); break;
-                case 2: units::inflate_tile<2, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 2, tx, ty, tz, dyn); break;
-                default: units::inflate_tile<3, 4, 8, 8, units::LoadL2, kInflateUnroll>(g, it.a.pl.occ_raw, it.a.pl.occ_inf, 3, tx, ty, tz, dyn); break;
-                }
+            switch (it.txw * 10 + it.tz) {
+            case 88: inflate_unit<8, 8>(it, tx, ty, tz, dyn); break;
+            case 84: inflate_unit<8, 4>(it, tx, ty, tz, dyn); break;
+            case 48: inflate_unit<4, 8>(it, tx, ty, tz, dyn); break;
+            default: inflate_unit<4, 4>(it, tx, ty, tz, dyn); break;
             }
         }
     }
@@ -200,7 +204,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
             i = next_item(items, n, 3, u, i);
             const BatchItem &it = items[i];
             const int64_t w = (u - it.off[3]) * kThreads + threadIdx.x;
-            if (it.loc_dst)
+            if (it.loc_dst && it.mwpu == 256)
+                units::merge_shift_unit<256, units::LoadL2, units::LoadL2>(
+                    it.a.g, it.a.pl, it.a.loc, it.loc_dst, it.dx, it.dy, it.dz, u - it.off[3],
+                    reinterpret_cast<uint8_t *>(dyn));
+            else if (it.loc_dst)
                 units::merge_shift_unit<kMergeWords, units::LoadL2, units::LoadL2>(
                     it.a.g, it.a.pl, it.a.loc, it.loc_dst, it.dx, it.dy, it.dz, u - it.off[3],
                     reinterpret_cast<uint8_t *>(dyn));

@@ -26,27 +26,13 @@ cudaError_t run(const FrameArgs &a, cudaStream_t s) {
                       a.pl.occ_inf, a.r);
 }
 
-// Tiles of 8 slices, or of 4 when a grid has between one and four 8-slice
-// tiles per SM: the shorter tiles stage more halo per word, but twice as
-// many CTAs share the device and the launch ends sooner.  Measured frame
-// times: a 200x200x100 grid (325 tiles of 8 slices) fell by about 2.3 us
-// with 650 of 4; an 80x80x40 grid (50 tiles, fewer than the SMs) rose by
-// 1.3 us, and a 400x400x120 grid (1500 tiles) did better with 8 slices.
-template <int TXW>
-cudaError_t run_r(const FrameArgs &a, cudaStream_t s, bool short_tiles) {
-    if (short_tiles) {
-        switch (a.r) {
-        case 1: return run<1, TXW, 8, 4>(a, s);
-        case 2: return run<2, TXW, 8, 4>(a, s);
-        case 3: return run<3, TXW, 8, 4>(a, s);
-        default: break;
-        }
-    }
+template <int TXW, int TZ>
+cudaError_t run_r(const FrameArgs &a, cudaStream_t s) {
     switch (a.r) {
-    case 1: return run<1, TXW, 8, 8>(a, s);
-    case 2: return run<2, TXW, 8, 8>(a, s);
-    case 3: return run<3, TXW, 8, 8>(a, s);
-    default: return run<0, TXW, 8, 8>(a, s);
+    case 1: return run<1, TXW, 8, TZ>(a, s);
+    case 2: return run<2, TXW, 8, TZ>(a, s);
+    case 3: return run<3, TXW, 8, TZ>(a, s);
+    default: return run<0, TXW, 8, 8>(a, s);   // other radii: 8-slice tiles, the radius at run time
     }
 }
 
@@ -75,13 +61,34 @@ cudaError_t configure_inflate() {
     return e;
 }
 
-cudaError_t launch_inflate(const FrameArgs &a, cudaStream_t s) {
-    // rows are a power of two of words, at least 4: 4-word tiles for narrow rows
-    const int txw = a.g.wx % 8 == 0 ? 8 : 4;
-    const int64_t tiles8 = (int64_t)((a.g.wx + txw - 1) / txw) * ((a.g.ny + 7) / 8) * ((a.g.nz + 7) / 8);
-    const int64_t sms = sms_of_current_device();
-    const bool short_tiles = tiles8 >= sms && tiles8 < 4 * sms;
-    return txw == 8 ? run_r<8>(a, s, short_tiles) : run_r<4>(a, s, short_tiles);
+// Tiles of 8 words (4 for rows of 4 words) by 8 rows by 8 slices, or 4
+// slices when a grid has between one and four 8-slice tiles per SM: the
+// shorter tiles stage more halo per word, but twice as many CTAs share the
+// device and the launch ends sooner.  Measured frame times: a 200x200x100
+// grid (325 tiles of 8 slices) fell by about 2.3 us with 650 of 4; an
+// 80x80x40 grid (50 tiles, fewer than the SMs) rose by 1.3 us, and a
+// 400x400x120 grid (1500 tiles) did better with 8 slices.  sc.inflate_tile
+// picks a shape instead (8-word tiles only where rows have a multiple of 8
+// words).
+cudaError_t launch_inflate(const FrameArgs &a, cudaStream_t s, const Sched &sc) {
+    // rows are a power of two of words, at least 4
+    const bool wide_ok = a.g.wx % 8 == 0;
+    int tile = sc.inflate_tile;
+    if (tile == kTileAuto) {
+        const int txw = wide_ok ? 8 : 4;
+        const int64_t tiles8 = (int64_t)((a.g.wx + txw - 1) / txw) * ((a.g.ny + 7) / 8) * ((a.g.nz + 7) / 8);
+        const int64_t sms = sms_of_current_device();
+        const bool short_tiles = tiles8 >= sms && tiles8 < 4 * sms;
+        tile = wide_ok ? (short_tiles ? kTile8x8x4 : kTile8x8x8) : (short_tiles ? kTile4x8x4 : kTile4x8x8);
+    }
+    if (!wide_ok && tile == kTile8x8x4) tile = kTile4x8x4;
+    if (!wide_ok && tile == kTile8x8x8) tile = kTile4x8x8;
+    switch (tile) {
+    case kTile4x8x4: return run_r<4, 4>(a, s);
+    case kTile4x8x8: return run_r<4, 8>(a, s);
+    case kTile8x8x4: return run_r<8, 4>(a, s);
+    default: return run_r<8, 8>(a, s);
+    }
 }
 
 }  // namespace vg

@@ -13,14 +13,14 @@ __global__ void __launch_bounds__(256) k_merge(const PlaneGeom g, Planes pl, uin
     units::merge_word<ALIGN8, units::LoadPlain, RL>(g, pl, loc, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <bool RL>
+template <bool RL, int WPU>
 __global__ void __launch_bounds__(256) k_merge_shift(const PlaneGeom g, Planes pl, const uint8_t *__restrict__ src,
                                                      uint8_t *__restrict__ dst, const int32_t dx, const int32_t dy,
                                                      const int32_t dz) {
-    __shared__ __align__(16) uint8_t sm[units::kMergeShiftSmem];
+    __shared__ __align__(16) uint8_t sm[units::merge_shift_smem(WPU)];
     pdl_trigger();
     pdl_wait();
-    units::merge_shift_unit<256, units::LoadRO, units::LoadPlain, RL>(g, pl, src, dst, dx, dy, dz, blockIdx.x, sm);
+    units::merge_shift_unit<WPU, units::LoadRO, units::LoadPlain, RL>(g, pl, src, dst, dx, dy, dz, blockIdx.x, sm);
 }
 
 // The literal loc_grid reading of Alg. 2: the occupied voxels of loc_grid,
@@ -71,14 +71,24 @@ cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s) {
     return launch_pdl(k_merge<false, false>, blocks, 256, 0, s, a.g, a.pl, a.loc);
 }
 
-cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s) {
-    const unsigned blocks = (unsigned)units::merge_shift_units<256>(a.g);
+template <int WPU>
+cudaError_t run_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s) {
+    const unsigned blocks = (unsigned)units::merge_shift_units<WPU>(a.g);
     if (blocks == 0) return cudaSuccess;
     if (a.lit & kLitRaysLast)
-        return launch_pdl(k_merge_shift<true>, blocks, 256, 0, s, a.g, a.pl, (const uint8_t *)a.loc, dst, delta[0],
-                          delta[1], delta[2]);
-    return launch_pdl(k_merge_shift<false>, blocks, 256, 0, s, a.g, a.pl, (const uint8_t *)a.loc, dst, delta[0],
-                      delta[1], delta[2]);
+        return launch_pdl(k_merge_shift<true, WPU>, blocks, 256, 0, s, a.g, a.pl, (const uint8_t *)a.loc, dst,
+                          delta[0], delta[1], delta[2]);
+    return launch_pdl(k_merge_shift<false, WPU>, blocks, 256, 0, s, a.g, a.pl, (const uint8_t *)a.loc, dst,
+                      delta[0], delta[1], delta[2]);
+}
+
+// One CTA per 256 plane words (8 KB of loc at most), or per 512
+// (sc.merge_words): a larger unit keeps more loads in flight per CTA, and
+// fewer CTAs share the device.
+cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s,
+                               const Sched &sc) {
+    if (sc.merge_words == 512) return run_merge_shift<512>(a, delta, dst, s);
+    return run_merge_shift<256>(a, delta, dst, s);
 }
 
 cudaError_t launch_loc_occupancy(const PlaneGeom &g, const uint8_t *loc, const int32_t delta[3], uint32_t *out,

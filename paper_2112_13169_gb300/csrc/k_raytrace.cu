@@ -54,13 +54,15 @@ cudaError_t configure_lpr(int dev, int idx) {
 }
 
 template <int LPR>
-cudaError_t launch_lpr(const FrameArgs &a, int idx, cudaStream_t s) {
+cudaError_t launch_lpr(const FrameArgs &a, int idx, cudaStream_t s, int ctas_per_sm) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const int64_t nrays = (2 * (int64_t)a.hw + 1) * (2 * (int64_t)a.hh + 1);
     const int64_t need = (nrays * LPR + kThreads - 1) / kThreads;
-    const int64_t resident = (int64_t)g_sms[dev] * (g_blocks_per_sm[dev][idx] > 0 ? g_blocks_per_sm[dev][idx] : 1);
+    int per_sm = g_blocks_per_sm[dev][idx] > 0 ? g_blocks_per_sm[dev][idx] : 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    const int64_t resident = (int64_t)g_sms[dev] * per_sm;
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
     if (blocks == 0) return cudaSuccess;
     // a packed visit holds a plane bit index below 2^31
@@ -95,16 +97,17 @@ int auto_lanes_per_ray(int32_t vd, int32_t hw, int32_t hh) {
     return 32;
 }
 
-cudaError_t launch_raytrace(const FrameArgs &a_in, int lanes_per_ray, cudaStream_t s) {
+cudaError_t launch_raytrace(const FrameArgs &a_in, int lanes_per_ray, cudaStream_t s, const Sched &sc) {
     FrameArgs a = a_in;
     if (!a.occ_test) a.occ_test = a.pl.occ_inf;   // the default reading: rays test the inflated plane
+    const int c = sc.rt_ctas;
     switch (lanes_per_ray) {
-    case 1: return launch_lpr<1>(a, 0, s);
-    case 2: return launch_lpr<2>(a, 1, s);
-    case 4: return launch_lpr<4>(a, 2, s);
-    case 8: return launch_lpr<8>(a, 3, s);
-    case 16: return launch_lpr<16>(a, 4, s);
-    case 32: return launch_lpr<32>(a, 5, s);
+    case 1: return launch_lpr<1>(a, 0, s, c);
+    case 2: return launch_lpr<2>(a, 1, s, c);
+    case 4: return launch_lpr<4>(a, 2, s, c);
+    case 8: return launch_lpr<8>(a, 3, s, c);
+    case 16: return launch_lpr<16>(a, 4, s, c);
+    case 32: return launch_lpr<32>(a, 5, s, c);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -28,6 +28,7 @@ struct vg_grid {
     int32_t origin[3];
     int32_t vd, hw, hh;
     int lanes_per_ray;
+    vg::Sched sched;      // tile and launch shapes of K2..K4 (vg_tune, vg_autotune)
     int device;
     uint8_t *base;        // the one device allocation
     uint8_t *loc;
@@ -57,6 +58,9 @@ struct vg_batch {
     int device;
     int ctas_per_sm;    // 0: occupancy limit
     int lanes;          // 0: each grid's own
+    int inflate_tz;     // inflate tile height in slices: 8 or 4
+    int merge_words;    // plane words per merge unit with a re-centre: 512 or 256
+    int spread;         // spread each frame's rays over proportionally more phase-3 units
     int64_t bar_ns;     // grid barrier time limit
     uint32_t bar_extra; // 1: the barrier waits for one CTA too many (tests its time limit)
     uint8_t *dev;       // BatchCtl followed by capacity BatchItems
@@ -256,7 +260,7 @@ cudaError_t apply_pending(vg_grid *G, cudaStream_t s) {
 cudaError_t finish_frame(vg_grid *G, FrameArgs &a, cudaStream_t s) {
     cudaError_t e;
     if (a.r > 0) {
-        e = launch(G, VG_K_INFLATE, s, [&] { return vg::launch_inflate(a, s); });
+        e = launch(G, VG_K_INFLATE, s, [&] { return vg::launch_inflate(a, s, G->sched); });
         if (e != cudaSuccess) return e;
     } else {
         a.pl.occ_inf = a.pl.occ_raw;   // no inflation: the raw plane is the inflated one
@@ -274,12 +278,12 @@ cudaError_t finish_frame(vg_grid *G, FrameArgs &a, cudaStream_t s) {
         a.occ_test = G->loc_occ;
     }
     const int lpr = G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh);
-    e = launch(G, VG_K_RAYTRACE, s, [&] { return vg::launch_raytrace(a, lpr, s); });
+    e = launch(G, VG_K_RAYTRACE, s, [&] { return vg::launch_raytrace(a, lpr, s, G->sched); });
     if (e != cudaSuccess) return e;
     if (!G->pend_on) return launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge(a, s); });
     // the measurement is in the re-centred frame: merge it over the shifted
     // grid, written whole into loc_alt
-    e = launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge_shift(a, G->pend, G->loc_alt, s); });
+    e = launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge_shift(a, G->pend, G->loc_alt, s, G->sched); });
     if (e != cudaSuccess) return e;
     std::swap(G->loc, G->loc_alt);
     G->pend_on = false;
@@ -420,7 +424,113 @@ int vg_tune(vg_grid *G, int32_t knob, int32_t value) {
         G->lanes_per_ray = value;
         return VG_OK;
     }
+    if (knob == VG_TUNE_INFLATE_TILE) {
+        if (value < VG_TILE_AUTO || value > VG_TILE_8x8x8) return VG_EINVAL;
+        G->sched.inflate_tile = value;
+        return VG_OK;
+    }
+    if (knob == VG_TUNE_RT_CTAS_PER_SM) {
+        if (value < 0 || value > 64) return VG_EINVAL;
+        G->sched.rt_ctas = value;
+        return VG_OK;
+    }
+    if (knob == VG_TUNE_MERGE_WORDS) {
+        if (value != 256 && value != 512) return VG_EINVAL;
+        G->sched.merge_words = value;
+        return VG_OK;
+    }
     return VG_EINVAL;
+}
+
+int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32_t height, int32_t dtype,
+                float depth_scale, const double T_wc[16], int32_t reps, void *stream, int32_t best[4]) {
+    if (!G || reps < 1 || reps > 1000) return VG_EINVAL;
+    DeviceGuard dg(G->device);
+    if (!dg.ok) return VG_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    // a re-centre pending at the start is applied first, so that every timed
+    // frame starts from the same grid; each timed frame then merges with a
+    // re-centre by zero (the identity), so that K4 runs the re-centring
+    // merge as it does when the robot moves every frame
+    cudaError_t e = apply_pending(G, s);
+    if (e != cudaSuccess) return status_of(e);
+    // every timed frame starts with a cold L2: a write of twice its size
+    int l2 = 0;
+    e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, G->device);
+    if (e != cudaSuccess) return status_of(e);
+    const size_t flush_bytes = 2 * (size_t)std::max(l2, 1 << 20);
+    void *flush = nullptr;
+    e = cudaMalloc(&flush, flush_bytes);
+    if (e != cudaSuccess) return status_of(e);
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    int rc = status_of(e);
+    // median event time of one frame under the grid's current schedule
+    auto time_setting = [&](float &med) -> int {
+        std::vector<float> ms((size_t)reps);
+        for (int r = -1; r < reps; ++r) {   // r = -1: untimed warm-up
+            if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, s) != cudaSuccess) return VG_ECUDA;
+            if (r >= 0 && cudaEventRecord(ev[2 * r], s) != cudaSuccess) return VG_ECUDA;
+            G->pend_on = true;
+            G->pend[0] = G->pend[1] = G->pend[2] = 0;
+            const int c = vg_integrate_depth(G, depth, mem, width, height, dtype, depth_scale, T_wc, stream);
+            if (c != VG_OK) return c;
+            if (r >= 0 && cudaEventRecord(ev[2 * r + 1], s) != cudaSuccess) return VG_ECUDA;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) return VG_ECUDA;
+        for (int r = 0; r < reps; ++r)
+            if (cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]) != cudaSuccess) return VG_ECUDA;
+        std::sort(ms.begin(), ms.end());
+        med = ms[(size_t)reps / 2];
+        return VG_OK;
+    };
+    // the schedule as it stands is the incumbent; coordinate descent then
+    // takes each knob in turn over its candidates, the others held at the
+    // best values so far, and a candidate replaces the incumbent only if it
+    // is at least 2 % faster (the timings' noise is about that)
+    const int tiles[4] = {VG_TILE_4x8x4, VG_TILE_4x8x8, VG_TILE_8x8x4, VG_TILE_8x8x8};
+    const int lanes[3] = {8, 16, 32};
+    const int ctas[5] = {1, 2, 3, 4, 5};
+    const int words[2] = {256, 512};
+    vg::Sched bs = G->sched;
+    int bl = G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh);
+    float best_ms = 0.0f;
+    G->lanes_per_ray = bl;
+    if (rc == VG_OK) rc = time_setting(best_ms);
+    for (int pass = 0; pass < 4 && rc == VG_OK; ++pass) {
+        const int n = pass == 0 ? 4 : (pass == 1 ? 3 : (pass == 2 ? 5 : 2));
+        if (pass == 0 && G->p.vox_inf == 0) continue;   // no K2 to tune
+        for (int i = 0; i < n && rc == VG_OK; ++i) {
+            vg::Sched sc = bs;
+            int lp = bl;
+            if (pass == 0) sc.inflate_tile = tiles[i];
+            if (pass == 1) lp = lanes[i];
+            if (pass == 2) sc.rt_ctas = ctas[i];
+            if (pass == 3) sc.merge_words = words[i];
+            G->sched = sc;
+            G->lanes_per_ray = lp;
+            float ms = 0.0f;
+            rc = time_setting(ms);
+            if (rc == VG_OK && ms < 0.98f * best_ms) {
+                best_ms = ms;
+                bs = sc;
+                bl = lp;
+            }
+        }
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    cudaStreamSynchronize(s);
+    cudaFree(flush);
+    G->sched = bs;
+    G->lanes_per_ray = bl;
+    if (best) {
+        best[0] = bs.inflate_tile;
+        best[1] = bl;
+        best[2] = bs.rt_ctas;
+        best[3] = bs.merge_words;
+    }
+    return rc;
 }
 
 int vg_integrate_depth(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32_t height,
@@ -569,6 +679,9 @@ int vg_batch_create(int32_t capacity, vg_batch **out) {
     vg_batch *B = new (std::nothrow) vg_batch();
     if (!B) return VG_ENOMEM;
     B->capacity = capacity;
+    B->inflate_tz = 8;
+    B->merge_words = vg::kBatchMergeWords;
+    B->spread = 1;
     B->bar_ns = vg::kBarrierNs;
     B->bytes = sizeof(vg::BatchCtl) + (size_t)capacity * sizeof(vg::BatchItem);
     cudaError_t e = cudaGetDevice(&B->device);
@@ -607,6 +720,21 @@ int vg_batch_tune(vg_batch *B, int32_t knob, int32_t value) {
     if (knob == VG_TUNE_BATCH_LANES) {
         if (value != 0 && value != 8 && value != 16 && value != 32) return VG_EINVAL;
         B->lanes = value;
+        return VG_OK;
+    }
+    if (knob == VG_TUNE_BATCH_INFLATE_SLICES) {
+        if (value != 0 && value != 4 && value != 8) return VG_EINVAL;
+        B->inflate_tz = value ? value : 8;
+        return VG_OK;
+    }
+    if (knob == VG_TUNE_BATCH_MERGE_WORDS) {
+        if (value != 0 && value != 256 && value != 512) return VG_EINVAL;
+        B->merge_words = value ? value : vg::kBatchMergeWords;
+        return VG_OK;
+    }
+    if (knob == VG_TUNE_BATCH_SPREAD) {
+        if (value != 0 && value != 1) return VG_EINVAL;
+        B->spread = value;
         return VG_OK;
     }
     if (knob == VG_TUNE_BATCH_BARRIER_US) {
@@ -682,9 +810,11 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
         int lpr = B->lanes ? B->lanes : (G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh));
         it.lpr = lpr < 8 ? 8 : lpr;
         it.txw = G->g.wx % 8 == 0 ? 8 : 4;
+        it.tz = B->inflate_tz;
+        it.mwpu = B->merge_words;
         it.tiles[0] = (G->g.wx + it.txw - 1) / it.txw;
         it.tiles[1] = (G->g.ny + 7) / 8;
-        it.tiles[2] = (G->g.nz + 7) / 8;
+        it.tiles[2] = (G->g.nz + it.tz - 1) / it.tz;
         it.align8 = (G->g.nx % 8 == 0 && reinterpret_cast<uintptr_t>(G->loc) % 8 == 0) ? 1 : 0;
         it.buffered = G->g.words < (int64_t(1) << 26) ? 1 : 0;
         const int64_t npix = (int64_t)f.width * f.height;
@@ -703,7 +833,7 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
             it.loc_dst = G->loc_alt;
             std::swap(G->loc, G->loc_alt);
             G->pend_on = false;
-            units[3] = (G->g.words + vg::kBatchMergeWords - 1) / vg::kBatchMergeWords;
+            units[3] = (G->g.words + it.mwpu - 1) / it.mwpu;
         }
         if (f.recentre) {
             // left pending, for the grid's next merge (or read)
@@ -725,8 +855,9 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
     // Phase 3 hands each CTA a contiguous run of units.  Unless the units
     // fill whole rounds of the grid, some CTAs would take one more unit
     // than others, so each frame's rays are spread over proportionally more
-    // (partly filled) units: G_i = ceil(groups_i * rounds * blocks / T).
-    {
+    // (partly filled) units: G_i = ceil(groups_i * rounds * blocks / T)
+    // (unless the spread is tuned off).
+    if (B->spread) {
         const int64_t T = total[2];
         const int64_t nb = batch_blocks(B);
         if (nb < 1) return VG_ECUDA;
@@ -794,7 +925,7 @@ int vg_batch_status(vg_batch *B) {
 }
 
 int vg_batch_autotune(vg_batch *B, const vg_frame *frames, int32_t n, int32_t reps, void *stream,
-                      int32_t best[2]) {
+                      int32_t best[5]) {
     if (!B || !frames || n < 1 || n > B->capacity || reps < 1) return VG_EINVAL;
     std::vector<vg_frame> fr(frames, frames + n);
     for (auto &f : fr) f.recentre = 0;
@@ -809,14 +940,33 @@ int vg_batch_autotune(vg_batch *B, const vg_frame *frames, int32_t n, int32_t re
     cudaError_t e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     if (e != cudaSuccess) return status_of(e);
-    const int lanes_c[4] = {0, 8, 16, 32};
+    // the knobs: CTAs per SM, lanes per ray, inflate tile slices, merge
+    // words per unit, phase-3 spread; coordinate descent, one knob at a time
+    // over its candidates with the others at the best values so far
+    int cur[5] = {B->ctas_per_sm ? B->ctas_per_sm : max_per_sm, B->lanes, B->inflate_tz, B->merge_words, B->spread};
+    std::vector<int> cand[5];
+    for (int c = 1; c <= max_per_sm; ++c) cand[0].push_back(c);
+    cand[1] = {0, 8, 16, 32};
+    cand[2] = {8, 4};
+    cand[3] = {512, 256};
+    cand[4] = {1, 0};
+    auto apply = [&](const int v[5]) {
+        B->ctas_per_sm = v[0];
+        B->lanes = v[1];
+        B->inflate_tz = v[2];
+        B->merge_words = v[3];
+        B->spread = v[4];
+    };
     float best_ms = 1e30f;
-    int best_c = 0, best_l = 0;
     int rc = VG_OK;
-    for (int c = 1; c <= max_per_sm && rc == VG_OK; ++c) {
-        for (int li = 0; li < 4 && rc == VG_OK; ++li) {
-            B->ctas_per_sm = c;
-            B->lanes = lanes_c[li];
+    for (int k = 0; k < 5 && rc == VG_OK; ++k) {
+        int pick[5];
+        std::memcpy(pick, cur, sizeof(pick));
+        for (size_t i = 0; i < cand[k].size() && rc == VG_OK; ++i) {
+            int v[5];
+            std::memcpy(v, cur, sizeof(v));
+            v[k] = cand[k][i];
+            apply(v);
             rc = vg_batch_step(B, fr.data(), n, stream);   // warm-up
             if (rc != VG_OK) break;
             e = cudaEventRecord(t0, s);
@@ -829,19 +979,16 @@ int vg_batch_autotune(vg_batch *B, const vg_frame *frames, int32_t n, int32_t re
             if (rc == VG_OK) rc = vg_batch_status(B);
             if (rc == VG_OK && ms < best_ms) {
                 best_ms = ms;
-                best_c = c;
-                best_l = lanes_c[li];
+                std::memcpy(pick, v, sizeof(pick));
             }
         }
+        std::memcpy(cur, pick, sizeof(cur));
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
-    B->ctas_per_sm = best_c;
-    B->lanes = best_l;
-    if (best) {
-        best[0] = best_c;
-        best[1] = best_l;
-    }
+    apply(cur);
+    if (best)
+        for (int k = 0; k < 5; ++k) best[k] = cur[k];
     return rc;
 }
 

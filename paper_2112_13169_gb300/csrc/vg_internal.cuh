@@ -109,6 +109,8 @@ struct BatchItem {
     int32_t vec;        // depth base aligned for 4-pixel loads
     int32_t lpr;        // K3 lanes per ray: 8, 16 or 32
     int32_t txw;        // inflate tile width in words: 4 or 8
+    int32_t tz;         // inflate tile height in slices: 4 or 8
+    int32_t mwpu;       // plane words per phase-4 unit of a merge with a re-centre: 256 or 512
     int32_t align8;     // loc rows and buffer allow 8-byte stores
     int32_t buffered;   // packed visits fit (plane words < 2^26)
     int32_t dx, dy, dz; // pending re-centre of the grid, applied by the merge
@@ -116,7 +118,8 @@ struct BatchItem {
 };
 
 // Plane words per phase-4 unit of a batch frame whose merge applies a
-// pending re-centre (other frames' units are 256 words, one per thread).
+// pending re-centre, unless tuned (other frames' units are 256 words, one
+// per thread).
 constexpr int kBatchMergeWords = 512;
 
 // Control block of a batch launch, copied to the device with the items.
@@ -139,17 +142,33 @@ inline __host__ __device__ int64_t plane_word(const PlaneGeom &g, int32_t x, int
     return ((int64_t)z * g.ny + y) * g.wx + (x >> 5);
 }
 
+// Schedule of the one-step kernels: tile shapes and launch shapes, none of
+// which changes a result (set with vg_tune, chosen by vg_autotune).
+enum {
+    kTileAuto = 0,   // K2 picks its tile from the grid's size
+    kTile4x8x4 = 1,  // K2 tile: words x rows x slices
+    kTile4x8x8 = 2,
+    kTile8x8x4 = 3,
+    kTile8x8x8 = 4
+};
+struct Sched {
+    int32_t inflate_tile = kTileAuto;
+    int32_t rt_ctas = 0;        // K3 CTAs per SM; 0: as many as fit
+    int32_t merge_words = 256;  // plane words per CTA of K4 with a re-centre: 256 or 512
+};
+
 // Kernel launchers (one translation unit each).
 cudaError_t launch_voxelize_depth(const FrameArgs &a, int32_t dtype, cudaStream_t s);
 cudaError_t launch_voxelize_points(const FrameArgs &a, cudaStream_t s);
 cudaError_t configure_inflate();   // once per device, before the first launch_inflate
-cudaError_t launch_inflate(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_inflate(const FrameArgs &a, cudaStream_t s, const Sched &sc = Sched());
 cudaError_t configure_raytrace(int dev);   // once per device, before the first launch_raytrace
 int auto_lanes_per_ray(int32_t vd, int32_t hw, int32_t hh);
-cudaError_t launch_raytrace(const FrameArgs &a, int lanes_per_ray, cudaStream_t s);
+cudaError_t launch_raytrace(const FrameArgs &a, int lanes_per_ray, cudaStream_t s, const Sched &sc = Sched());
 cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s);
 // K4 over a pending re-centre: reads a.loc shifted by delta, writes every voxel of dst
-cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s);
+cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s,
+                               const Sched &sc = Sched());
 cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8_t *src,
                          uint8_t *dst, cudaStream_t s);
 // loc_grid's occupied voxels after a re-centre by delta, as a bit plane

@@ -32,10 +32,14 @@ EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points
            "vg_batch_create", "vg_batch_destroy", "vg_batch_prepare", "vg_batch_enqueue", "vg_batch_step",
            "vg_batch_status", "vg_batch_tune", "vg_batch_autotune", "vg_server_create", "vg_server_destroy",
            "vg_server_add_camera", "vg_server_remove_camera", "vg_server_submit", "vg_server_wait",
-           "vg_server_read", "vg_server_stats", "vg_server_ticket_times")
+           "vg_server_read", "vg_server_stats", "vg_server_ticket_times", "vg_autotune")
 VG_TUNE_BATCH_CTAS_PER_SM, VG_TUNE_BATCH_LANES, VG_TUNE_BATCH_BARRIER_US, VG_TUNE_BATCH_BARRIER_EXTRA = 100, 101, 102, 103
+VG_TUNE_BATCH_INFLATE_SLICES, VG_TUNE_BATCH_MERGE_WORDS, VG_TUNE_BATCH_SPREAD = 104, 105, 106
 KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift", "loc_occupancy")
-VG_TUNE_RT_LANES = 0
+VG_TUNE_RT_LANES, VG_TUNE_INFLATE_TILE, VG_TUNE_RT_CTAS_PER_SM, VG_TUNE_MERGE_WORDS = 0, 1, 2, 3
+VG_TILE_AUTO, VG_TILE_4x8x4, VG_TILE_4x8x8, VG_TILE_8x8x4, VG_TILE_8x8x8 = range(5)
+TILE_NAMES = {VG_TILE_AUTO: "auto", VG_TILE_4x8x4: "4x8x4", VG_TILE_4x8x8: "4x8x8", VG_TILE_8x8x4: "8x8x4",
+              VG_TILE_8x8x8: "8x8x8"}
 
 
 class vg_params(C.Structure):
@@ -101,6 +105,7 @@ def load(path=None):
         "vg_profile_enable": (C.c_int, [vp, i32]),
         "vg_profile_read": (C.c_int, [vp, vp, vp, vp, i32]),
         "vg_tune": (C.c_int, [vp, i32, i32]),
+        "vg_autotune": (C.c_int, [vp, vp, i32, i32, i32, i32, f32, vp, i32, vp, vp]),
         "vg_strerror": (C.c_char_p, [C.c_int]),
         "vg_integrate_depth_noalloc": (C.c_int, [vp, vp, vp, vp, i32, i32, i32, f32, vp, vp]),
         "vg_batch_create": (C.c_int, [i32, C.POINTER(vp)]),
@@ -395,6 +400,21 @@ class Grid:
     def tune(self, lanes_per_ray):
         vg_tune(self.h, VG_TUNE_RT_LANES, lanes_per_ray)
 
+    def set(self, knob, value):
+        vg_tune(self.h, knob, value)
+
+    def autotune(self, depth, T_wc, depth_scale=1.0, reps=5, stream=None):
+        """Times the schedule knobs on this frame and keeps the fastest;
+        returns {"tile", "lanes", "ctas_per_sm", "merge_words"}."""
+        ptr, mem, nbytes, dt = _buffer(depth)
+        dtype = _depth_dtype(dt)
+        H, W = depth.shape
+        T, tp = _f64(T_wc, 16)
+        best = (C.c_int32 * 4)()
+        _check(load().vg_autotune(self.h, ptr, mem, W, H, dtype, float(depth_scale), tp, int(reps), _stream(stream),
+                                  best), "vg_autotune")
+        return {"tile": TILE_NAMES[best[0]], "lanes": best[1], "ctas_per_sm": best[2], "merge_words": best[3]}
+
     def close(self):
         if self.h:
             vg_destroy(self.h)
@@ -461,11 +481,13 @@ class Batch:
         _check(load().vg_batch_tune(self.h, int(knob), int(value)), "vg_batch_tune")
 
     def autotune(self, frames, reps=3, stream=None):
+        """The batch autotuner; returns {"ctas_per_sm", "lanes", "inflate_slices",
+        "merge_words", "spread"} (lanes 0: each grid's own)."""
         arr = make_frames(frames)
-        best = (C.c_int32 * 2)()
+        best = (C.c_int32 * 5)()
         _check(load().vg_batch_autotune(self.h, arr, len(frames), int(reps), _stream(stream), best),
                "vg_batch_autotune")
-        return int(best[0]), int(best[1])
+        return dict(zip(("ctas_per_sm", "lanes", "inflate_slices", "merge_words", "spread"), (int(v) for v in best)))
 
     def close(self):
         if self.h:

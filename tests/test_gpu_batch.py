@@ -185,8 +185,9 @@ def test_autotune_keeps_results(vg):
     ws = [make("robot", robot=i, frames=2) for i in range(20, 24)]
     R = Robots(vg, ws)
     batch = vg.Batch(4)
-    ctas, lanes = batch.autotune(R.frames(0), reps=2)
-    assert ctas >= 1 and lanes in (0, 8, 16, 32)
+    best = batch.autotune(R.frames(0), reps=2)
+    assert best["ctas_per_sm"] >= 1 and best["lanes"] in (0, 8, 16, 32)
+    assert best["inflate_slices"] in (4, 8) and best["merge_words"] in (256, 512) and best["spread"] in (0, 1)
     # the autotuner merged frame 0 without re-centring; so does the oracle
     R.oracle_step(0, recentre=False)
     R.check("after autotune")
@@ -194,6 +195,25 @@ def test_autotune_keeps_results(vg):
     assert batch.status() == vg.VG_OK
     R.oracle_step(1)
     R.check("after a tuned step")
+    batch.close()
+    R.close()
+
+
+@pytest.mark.parametrize("slices,words,spread,ctas", [(4, 256, 0, 1), (4, 512, 1, 2), (8, 256, 1, 3)])
+def test_batch_schedule_knobs_keep_results(vg, slices, words, spread, ctas):
+    # every schedule the batch autotuner can pick gives the oracle's grids
+    ws = [make("robot", robot=i, frames=2) for i in (0, 7, 12, 23)]   # vox_inf 1-3, 848x480, 640x480
+    R = Robots(vg, ws)
+    batch = vg.Batch(4)
+    batch.tune(vg.VG_TUNE_BATCH_INFLATE_SLICES, slices)
+    batch.tune(vg.VG_TUNE_BATCH_MERGE_WORDS, words)
+    batch.tune(vg.VG_TUNE_BATCH_SPREAD, spread)
+    batch.tune(vg.VG_TUNE_BATCH_CTAS_PER_SM, ctas)
+    for step in range(2):
+        batch.step(R.frames(step))
+        assert batch.status() == vg.VG_OK
+        R.oracle_step(step)
+        R.check("schedule %s step %d" % ((slices, words, spread, ctas), step))
     batch.close()
     R.close()
 

@@ -127,6 +127,43 @@ def test_hires_u16_full_size(vg):
     run_workload(vg, make("hires"), 50)
 
 
+@pytest.mark.parametrize("tile", [1, 2, 3, 4])
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_schedule_knobs_keep_results(vg, tile, r):
+    # every schedule the per-grid autotuner can pick: the four inflate tiles
+    # at radii 1-3 (on a grid with 8-word rows, so 8-word tiles are used),
+    # K3 capped at few CTAs per SM, and K4's 512-word units with re-centres
+    w = make("robot", robot=90 + r, frames=3, spec=(640, 480, 0.05, (256, 120, 60), r))
+    g = w.grid
+    P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos)
+    P.g.set(vg.VG_TUNE_INFLATE_TILE, tile)
+    P.g.set(vg.VG_TUNE_RT_CTAS_PER_SM, tile)          # 1..4 CTAs per SM
+    P.g.set(vg.VG_TUNE_MERGE_WORDS, 512 if tile % 2 else 256)
+    for f in w.frames:
+        P.depth(f.depth, f.T_wc, check=False)
+        P.check("tile %d r %d frame" % (tile, r))
+        P.shift(f.robot_pos, check=False)
+    P.check("after the last re-centre")
+    P.close()
+
+
+def test_autotune_picks_a_schedule_and_keeps_results(vg):
+    w = make("seq", frames=3)
+    g = w.grid
+    P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos)
+    d0 = torch.from_numpy(w.frames[0].depth).cuda()
+    best = P.g.autotune(d0, w.frames[0].T_wc, reps=2)
+    assert best["tile"] in ("auto", "4x8x4", "4x8x8", "8x8x4", "8x8x8") and best["lanes"] in (8, 16, 32)
+    assert 0 <= best["ctas_per_sm"] <= 5 and best["merge_words"] in (256, 512)
+    # the tuner merged frame 0 (over re-centres by zero); so does the oracle
+    P.o.integrate_depth(w.frames[0].T_wc, w.frames[0].depth)
+    P.check("after autotune")
+    for f in w.frames[1:]:
+        P.depth(f.depth, f.T_wc, check=False)
+        P.shift(f.robot_pos)
+    P.close()
+
+
 @pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8, 16, 32])
 def test_lanes_per_ray_do_not_change_results(vg, lanes):
     # 0 is automatic; 1, 2 and 4 lanes overflow the per-lane visit buffer on
@@ -392,6 +429,23 @@ def test_point_clouds(vg):
     P.points(pts[:1], body_pose([0.01, 0.02, 0.03], -0.4))
     P.points(np.zeros((0, 3), np.float32), body_pose([0.01, 0.02, 0.03], 2.0))
     P.points(pts, body_pose([0.01, 0.02, 0.03], 1.0), device=False)
+    P.close()
+
+
+@pytest.mark.parametrize("npts", [300000, 1000000])
+def test_point_clouds_at_scale(vg, npts):
+    # dense clouds as in the paper's populate sweep (Fig. 4a: up to 300,000
+    # points; here also 1,000,000), uniform in the field of view up to the
+    # range, on the paper's standard grid; with a re-centre between frames
+    rng = np.random.default_rng(23 + npts)
+    P = Pair(vg, (100, 100, 20), 0.15, 85.0, 101.0, 6.5, 2, (7.5, 7.5, 1.4))
+    for k in range(2):
+        z = rng.uniform(0.3, 6.5, npts)
+        tx, ty = np.tan(np.radians(85.0 / 2)), np.tan(np.radians(101.0 / 2))
+        pts = np.stack([rng.uniform(-tx, tx, npts) * z, rng.uniform(-ty, ty, npts) * z, z], 1).astype(np.float32)
+        pos = np.array([7.5 + 0.3 * k, 7.5 - 0.2 * k, 1.4])
+        P.points(pts, body_pose(pos, 0.3 + 0.5 * k, 0.05))
+        P.shift(pos + np.array([0.4, 0.1, 0.0]))
     P.close()
 
 
