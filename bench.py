@@ -693,7 +693,8 @@ def run_ours(args):
         grid.close()
         tiles = {v: k for k, v in vg.TILE_NAMES.items()}
         sched.update({vg.VG_TUNE_INFLATE_TILE: tiles[best["tile"]], vg.VG_TUNE_RT_LANES: best["lanes"],
-                      vg.VG_TUNE_RT_CTAS_PER_SM: best["ctas_per_sm"], vg.VG_TUNE_MERGE_WORDS: best["merge_words"]})
+                      vg.VG_TUNE_RT_CTAS_PER_SM: best["ctas_per_sm"], vg.VG_TUNE_MERGE_WORDS: best["merge_words"],
+                      vg.VG_TUNE_INFLATE_TMA: best["inflate_tma"]})
         tune_info = {"schedule": best}
 
     # ---- timed region: per-frame device time ------------------------------
@@ -717,21 +718,27 @@ def run_ours(args):
     grid.close()
 
     if tune_info is not None:
-        # the same steps with the library's default schedule
-        grid = new_grid(tuned=False)
-        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        # the tuned and the default schedule over the same steps, frames
+        # alternating between a grid of each (so drifts hit both alike)
+        gt, gd = new_grid(), new_grid(tuned=False)
+        ev2 = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+               for _ in range(2)]
         for k in range(args.steps):
-            flush.zero_()
-            ev2[k][0].record(stream)
-            step(grid, k)
-            ev2[k][1].record(stream)
+            for j, gr in enumerate((gt, gd)):
+                flush.zero_()
+                ev2[j][k][0].record(stream)
+                step(gr, k)
+                ev2[j][k][1].record(stream)
         torch.cuda.synchronize()
-        grid.close()
-        lat0 = np.array([a.elapsed_time(b) for a, b in ev2])
-        tune_info["default_schedule_latency_ms"] = {"p50": float(np.percentile(lat0, 50)),
-                                                    "p99": float(np.percentile(lat0, 99)),
-                                                    "mean": float(lat0.mean())}
-        tune_info["gain_mean"] = float(lat0.mean() / lat_ms.mean())
+        gt.close()
+        gd.close()
+        for j, name in enumerate(("tuned", "default")):
+            l2 = np.array([a.elapsed_time(b) for a, b in ev2[j]])
+            tune_info["alternating_%s_latency_ms" % name] = {"p50": float(np.percentile(l2, 50)),
+                                                             "p99": float(np.percentile(l2, 99)),
+                                                             "mean": float(l2.mean())}
+        tune_info["gain_mean"] = (tune_info["alternating_default_latency_ms"]["mean"] /
+                                  tune_info["alternating_tuned_latency_ms"]["mean"])
 
     total_s = float(lat_ms.sum()) / 1e3
     total_s_max = dist.max(total_s)

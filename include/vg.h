@@ -130,6 +130,9 @@ typedef struct {
     uint64_t frames;          /* vg_integrate_* calls */
     uint64_t points_in_grid;  /* valid points that landed inside the grid (K1) */
     uint64_t ray_visits;      /* in-grid voxel visits over all rays (K3) */
+    uint64_t wait_timeouts;   /* device waits for a tile copy (K2) that ran out on the grid's
+                                 device since the library was loaded, any grid; the tile was
+                                 left unwritten (counted with or without VG_FLAG_STATS) */
 } vg_stats_t;
 
 /*
@@ -514,30 +517,36 @@ VG_API int vg_profile_read(vg_grid *grid, double ms[VG_NKERNELS], int64_t timed[
  *  VG_TUNE_MERGE_WORDS
  *                    plane words per CTA of K4 when it applies a pending
  *                    re-centre: 256 (default) or 512.
+ *  VG_TUNE_INFLATE_TMA
+ *                    1 (default): K2 moves each tile's raw words with one
+ *                    tensor-memory-accelerator copy (radius 1..3); 0: its
+ *                    threads load them.
  * Results do not depend on any of them.  Errors: VG_EINVAL.
  */
 enum {
     VG_TUNE_RT_LANES = 0,
     VG_TUNE_INFLATE_TILE = 1,
     VG_TUNE_RT_CTAS_PER_SM = 2,
-    VG_TUNE_MERGE_WORDS = 3
+    VG_TUNE_MERGE_WORDS = 3,
+    VG_TUNE_INFLATE_TMA = 4
 };
 enum { VG_TILE_AUTO = 0, VG_TILE_4x8x4 = 1, VG_TILE_4x8x8 = 2, VG_TILE_8x8x4 = 3, VG_TILE_8x8x8 = 4 };
 VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
 
 /*
- * Autotuner of the per-frame kernels' schedule.  Measures the median CUDA
- * event time of `reps` (1 .. 1000) measurements of the given depth frame
- * (arguments as for vg_integrate_depth), each starting with a cold L2 (a
- * write of twice the L2's size to a scratch buffer the call allocates and
- * frees), first under the grid's schedule as it stands, then for each
- * candidate value of one knob at a time -- K2's tile (the four shapes),
- * K3's lanes per ray (8, 16, 32), K3's CTAs per SM (1..5) and K4's words
- * per CTA (256, 512) -- with the other knobs at the best values found so
- * far; a candidate wins only if it is at least 2 % faster.  Keeps the
- * winning schedule in the grid and writes it to best[4] = {tile, lanes,
- * ctas_per_sm, merge_words} (tile VG_TILE_AUTO and ctas_per_sm 0 where the
- * defaults won; may be NULL).  Each timed measurement merges the frame over
+ * Autotuner of the per-frame kernels' schedule.  Starting from the grid's
+ * schedule as it stands, it takes one knob at a time -- K2's tile (the four
+ * shapes), K3's lanes per ray (8, 16, 32), K3's CTAs per SM (1..5), K4's
+ * words per CTA (256, 512) and K2's staging (tensor copies or threads) --
+ * and compares each candidate value with the best schedule so far: `reps`
+ * (1 .. 1000) measurements of the given depth frame (arguments as for
+ * vg_integrate_depth) under each, alternating, every one starting with a
+ * cold L2 (a write of twice the L2's size to a scratch buffer the call
+ * allocates and frees); the candidate wins only if its median CUDA event
+ * time is at least 2 % below the incumbent's.  Keeps the winning schedule in the grid and writes
+ * it to best[5] = {tile, lanes, ctas_per_sm, merge_words, inflate_tma}
+ * (tile VG_TILE_AUTO and ctas_per_sm 0 where the defaults won; may be
+ * NULL).  Each timed measurement merges the frame over
  * a re-centre by zero, so K4 runs the re-centring merge that a moving
  * robot's frames take; merging the same measurement again leaves the grid
  * as one merge leaves it.  A re-centre pending at the call is applied
@@ -546,7 +555,7 @@ VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
  */
 VG_API int vg_autotune(vg_grid *grid, const void *depth, int32_t mem, int32_t width, int32_t height,
                        int32_t dtype, float depth_scale, const double T_wc[16], int32_t reps, void *stream,
-                       int32_t best[4]);
+                       int32_t best[5]);
 
 /*
  * One measurement without any device allocation.  The paper has no

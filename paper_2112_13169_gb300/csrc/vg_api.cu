@@ -439,11 +439,16 @@ int vg_tune(vg_grid *G, int32_t knob, int32_t value) {
         G->sched.merge_words = value;
         return VG_OK;
     }
+    if (knob == VG_TUNE_INFLATE_TMA) {
+        if (value != 0 && value != 1) return VG_EINVAL;
+        G->sched.inflate_tma = value;
+        return VG_OK;
+    }
     return VG_EINVAL;
 }
 
 int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32_t height, int32_t dtype,
-                float depth_scale, const double T_wc[16], int32_t reps, void *stream, int32_t best[4]) {
+                float depth_scale, const double T_wc[16], int32_t reps, void *stream, int32_t best[5]) {
     if (!G || reps < 1 || reps > 1000) return VG_EINVAL;
     DeviceGuard dg(G->device);
     if (!dg.ok) return VG_ECUDA;
@@ -462,44 +467,60 @@ int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32
     void *flush = nullptr;
     e = cudaMalloc(&flush, flush_bytes);
     if (e != cudaSuccess) return status_of(e);
-    std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+    std::vector<cudaEvent_t> ev(4 * (size_t)reps, nullptr);
     for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
     int rc = status_of(e);
-    // median event time of one frame under the grid's current schedule
-    auto time_setting = [&](float &med) -> int {
+    // One measurement under a schedule, events e0/e1 around it (none when
+    // NULL), after the L2 flush.
+    auto frame = [&](const vg::Sched &sc, int lp, cudaEvent_t e0, cudaEvent_t e1) -> int {
+        G->sched = sc;
+        G->lanes_per_ray = lp;
+        if (cudaMemsetAsync(flush, 0, flush_bytes, s) != cudaSuccess) return VG_ECUDA;
+        if (e0 && cudaEventRecord(e0, s) != cudaSuccess) return VG_ECUDA;
+        G->pend_on = true;
+        G->pend[0] = G->pend[1] = G->pend[2] = 0;
+        const int c = vg_integrate_depth(G, depth, mem, width, height, dtype, depth_scale, T_wc, stream);
+        if (c != VG_OK) return c;
+        if (e1 && cudaEventRecord(e1, s) != cudaSuccess) return VG_ECUDA;
+        return VG_OK;
+    };
+    auto median = [&](size_t first) -> float {
         std::vector<float> ms((size_t)reps);
-        for (int r = -1; r < reps; ++r) {   // r = -1: untimed warm-up
-            if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, s) != cudaSuccess) return VG_ECUDA;
-            if (r >= 0 && cudaEventRecord(ev[2 * r], s) != cudaSuccess) return VG_ECUDA;
-            G->pend_on = true;
-            G->pend[0] = G->pend[1] = G->pend[2] = 0;
-            const int c = vg_integrate_depth(G, depth, mem, width, height, dtype, depth_scale, T_wc, stream);
+        for (int r = 0; r < reps; ++r)
+            if (cudaEventElapsedTime(&ms[r], ev[first + 4 * r], ev[first + 4 * r + 1]) != cudaSuccess) return -1.0f;
+        std::sort(ms.begin(), ms.end());
+        return ms[(size_t)reps / 2];
+    };
+    // Whether candidate (sc, lp) is at least 2 % faster than the incumbent
+    // (bs, bl): their frames alternate, so that drifts of the clock or of
+    // the host hit both alike, and their median event times are compared.
+    auto better = [&](const vg::Sched &bs, int bl, const vg::Sched &sc, int lp, bool &win) -> int {
+        for (int r = -1; r < reps; ++r) {   // r = -1: untimed warm-up of both
+            const size_t k = 4 * (size_t)(r < 0 ? 0 : r);
+            int c = frame(bs, bl, r < 0 ? nullptr : ev[k], r < 0 ? nullptr : ev[k + 1]);
+            if (c == VG_OK) c = frame(sc, lp, r < 0 ? nullptr : ev[k + 2], r < 0 ? nullptr : ev[k + 3]);
             if (c != VG_OK) return c;
-            if (r >= 0 && cudaEventRecord(ev[2 * r + 1], s) != cudaSuccess) return VG_ECUDA;
         }
         if (cudaStreamSynchronize(s) != cudaSuccess) return VG_ECUDA;
-        for (int r = 0; r < reps; ++r)
-            if (cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]) != cudaSuccess) return VG_ECUDA;
-        std::sort(ms.begin(), ms.end());
-        med = ms[(size_t)reps / 2];
+        const float mi = median(0), mc = median(2);
+        if (mi < 0.0f || mc < 0.0f) return VG_ECUDA;
+        win = mc < 0.98f * mi;
         return VG_OK;
     };
     // the schedule as it stands is the incumbent; coordinate descent then
     // takes each knob in turn over its candidates, the others held at the
     // best values so far, and a candidate replaces the incumbent only if it
-    // is at least 2 % faster (the timings' noise is about that)
+    // is at least 2 % faster in an alternating comparison
     const int tiles[4] = {VG_TILE_4x8x4, VG_TILE_4x8x8, VG_TILE_8x8x4, VG_TILE_8x8x8};
     const int lanes[3] = {8, 16, 32};
     const int ctas[5] = {1, 2, 3, 4, 5};
     const int words[2] = {256, 512};
+    const int tma[2] = {1, 0};
     vg::Sched bs = G->sched;
     int bl = G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh);
-    float best_ms = 0.0f;
-    G->lanes_per_ray = bl;
-    if (rc == VG_OK) rc = time_setting(best_ms);
-    for (int pass = 0; pass < 4 && rc == VG_OK; ++pass) {
+    for (int pass = 0; pass < 5 && rc == VG_OK; ++pass) {
         const int n = pass == 0 ? 4 : (pass == 1 ? 3 : (pass == 2 ? 5 : 2));
-        if (pass == 0 && G->p.vox_inf == 0) continue;   // no K2 to tune
+        if ((pass == 0 || pass == 4) && G->p.vox_inf == 0) continue;   // no K2 to tune
         for (int i = 0; i < n && rc == VG_OK; ++i) {
             vg::Sched sc = bs;
             int lp = bl;
@@ -507,12 +528,11 @@ int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32
             if (pass == 1) lp = lanes[i];
             if (pass == 2) sc.rt_ctas = ctas[i];
             if (pass == 3) sc.merge_words = words[i];
-            G->sched = sc;
-            G->lanes_per_ray = lp;
-            float ms = 0.0f;
-            rc = time_setting(ms);
-            if (rc == VG_OK && ms < 0.98f * best_ms) {
-                best_ms = ms;
+            if (pass == 4) sc.inflate_tma = tma[i];
+            if (std::memcmp(&sc, &bs, sizeof(sc)) == 0 && lp == bl) continue;   // the incumbent itself
+            bool win = false;
+            rc = better(bs, bl, sc, lp, win);
+            if (rc == VG_OK && win) {
                 bs = sc;
                 bl = lp;
             }
@@ -529,6 +549,7 @@ int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32
         best[1] = bl;
         best[2] = bs.rt_ctas;
         best[3] = bs.merge_words;
+        best[4] = bs.inflate_tma;
     }
     return rc;
 }
@@ -666,9 +687,13 @@ int vg_stats(vg_grid *G, vg_stats_t *out) {
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(h, G->stats, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return status_of(e);
+    unsigned waits = 0;
+    e = vg::wait_timeouts(&waits);
+    if (e != cudaSuccess) return status_of(e);
     out->frames = G->frames;
     out->points_in_grid = h[1];
     out->ray_visits = h[2];
+    out->wait_timeouts = waits;
     return VG_OK;
 }
 

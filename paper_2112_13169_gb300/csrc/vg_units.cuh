@@ -204,7 +204,59 @@ __host__ __device__ constexpr size_t inflate_smem_words(int r) {
     return (size_t)(TZ + 2 * r) * (TY + 2 * r) * (TXW + 2) + (size_t)(TZ + 2 * r) * (TY + 2 * r) * TXW;
 }
 
+// The x, y and z passes of a tile whose raw words are staged in shared
+// memory: word w0 - 1 + lx of row y0 - r + ly, slice z0 - r + lz at
+// st[(lz * hy + ly) * sx + ox + lx], lx in [0, TXW + 2), with zeros outside
+// the grid.  buf1 (hz * hy * TXW words) must not overlap the staged words;
+// the y pass reuses the staged words' memory.  CTA-cooperative (256
+// threads); ends with a barrier.
+template <int R, int TXW, int TY, int TZ>
+__device__ __forceinline__ void inflate_passes(const PlaneGeom &g, uint32_t *out, const int r_rt, int tile_x,
+                                               int tile_y, int tile_z, uint32_t *st, int sx, int ox, uint32_t *buf1) {
+    const int r = R > 0 ? R : r_rt;
+    const int hy = TY + 2 * r, hz = TZ + 2 * r;
+    const int w0 = tile_x * TXW, y0 = tile_y * TY, z0 = tile_z * TZ;
+
+    // x pass, clearing bits past the end of the row
+    const int n1 = hz * hy * TXW;
+    for (int i = threadIdx.x; i < n1; i += 256) {
+        const int lx = i % TXW, row = i / TXW;
+        const uint32_t *b = st + row * sx + ox + lx;
+        uint32_t v = dilate_x(b[0], b[1], b[2], r);
+        const int valid = g.nx - 32 * (w0 + lx);
+        if (valid < 32) v &= valid > 0 ? ((1u << valid) - 1u) : 0u;
+        buf1[i] = v;
+    }
+    __syncthreads();
+
+    // y pass into the staged words' memory (now free): hz * TY * TXW
+    uint32_t *buf2 = st;
+    const int n2 = hz * TY * TXW;
+    for (int i = threadIdx.x; i < n2; i += 256) {
+        const int lx = i % TXW, rest = i / TXW, ly = rest % TY, lz = rest / TY;
+        const uint32_t *b = buf1 + (lz * hy + ly) * TXW + lx;
+        uint32_t v = 0;
+        for (int d = 0; d <= 2 * r; ++d) v |= b[d * TXW];
+        buf2[i] = v;
+    }
+    __syncthreads();
+
+    // z pass to global
+    constexpr int n3 = TZ * TY * TXW;
+    for (int i = threadIdx.x; i < n3; i += 256) {
+        const int lx = i % TXW, rest = i / TXW, ly = rest % TY, lz = rest / TY;
+        const int w = w0 + lx, y = y0 + ly, z = z0 + lz;
+        if (w >= g.wx || y >= g.ny || z >= g.nz) continue;
+        const uint32_t *b = buf2 + (lz * TY + ly) * TXW + lx;
+        uint32_t v = 0;
+        for (int d = 0; d <= 2 * r; ++d) v |= b[d * TY * TXW];
+        out[((int64_t)z * g.ny + y) * g.wx + w] = v;
+    }
+    __syncthreads();   // the tile's shared memory may be reused right away
+}
+
 // CTA-cooperative: every thread of the (256-thread) CTA must call this.
+// The threads stage the tile's raw words with halo themselves.
 template <int R, int TXW, int TY, int TZ, class L, int STAGE_UNROLL = 8>
 __device__ __forceinline__ void inflate_tile(const PlaneGeom &g, const uint32_t *raw, uint32_t *out, const int r_rt,
                                              int tile_x, int tile_y, int tile_z, uint32_t *sm) {
@@ -214,7 +266,7 @@ __device__ __forceinline__ void inflate_tile(const PlaneGeom &g, const uint32_t 
     uint32_t *buf1 = sm + hz * hy * hx;           // hz * hy * TXW: x-dilated
     const int w0 = tile_x * TXW, y0 = tile_y * TY, z0 = tile_z * TZ;
 
-    // 1. stage raw words (zero outside the grid)
+    // stage raw words (zero outside the grid)
     const int n0 = hz * hy * hx;
 #pragma unroll STAGE_UNROLL
     for (int i = threadIdx.x; i < n0; i += 256) {
@@ -226,42 +278,7 @@ __device__ __forceinline__ void inflate_tile(const PlaneGeom &g, const uint32_t 
         buf0[i] = v;
     }
     __syncthreads();
-
-    // 2. x pass, clearing bits past the end of the row
-    const int n1 = hz * hy * TXW;
-    for (int i = threadIdx.x; i < n1; i += 256) {
-        const int lx = i % TXW, row = i / TXW;
-        const uint32_t *b = buf0 + row * hx + lx;
-        uint32_t v = dilate_x(b[0], b[1], b[2], r);
-        const int valid = g.nx - 32 * (w0 + lx);
-        if (valid < 32) v &= valid > 0 ? ((1u << valid) - 1u) : 0u;
-        buf1[i] = v;
-    }
-    __syncthreads();
-
-    // 3. y pass into buf0 (now free): hz * TY * TXW
-    const int n2 = hz * TY * TXW;
-    for (int i = threadIdx.x; i < n2; i += 256) {
-        const int lx = i % TXW, rest = i / TXW, ly = rest % TY, lz = rest / TY;
-        const uint32_t *b = buf1 + (lz * hy + ly) * TXW + lx;
-        uint32_t v = 0;
-        for (int d = 0; d <= 2 * r; ++d) v |= b[d * TXW];
-        buf0[i] = v;
-    }
-    __syncthreads();
-
-    // 4. z pass to global
-    constexpr int n3 = TZ * TY * TXW;
-    for (int i = threadIdx.x; i < n3; i += 256) {
-        const int lx = i % TXW, rest = i / TXW, ly = rest % TY, lz = rest / TY;
-        const int w = w0 + lx, y = y0 + ly, z = z0 + lz;
-        if (w >= g.wx || y >= g.ny || z >= g.nz) continue;
-        const uint32_t *b = buf0 + (lz * TY + ly) * TXW + lx;
-        uint32_t v = 0;
-        for (int d = 0; d <= 2 * r; ++d) v |= b[d * TY * TXW];
-        out[((int64_t)z * g.ny + y) * g.wx + w] = v;
-    }
-    __syncthreads();   // the tile's shared memory may be reused right away
+    inflate_passes<R, TXW, TY, TZ>(g, out, r_rt, tile_x, tile_y, tile_z, buf0, hx, 0, buf1);
 }
 
 // ---------------------------------------------------------------------------

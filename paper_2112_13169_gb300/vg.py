@@ -36,7 +36,7 @@ EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points
 VG_TUNE_BATCH_CTAS_PER_SM, VG_TUNE_BATCH_LANES, VG_TUNE_BATCH_BARRIER_US, VG_TUNE_BATCH_BARRIER_EXTRA = 100, 101, 102, 103
 VG_TUNE_BATCH_INFLATE_SLICES, VG_TUNE_BATCH_MERGE_WORDS, VG_TUNE_BATCH_SPREAD = 104, 105, 106
 KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift", "loc_occupancy")
-VG_TUNE_RT_LANES, VG_TUNE_INFLATE_TILE, VG_TUNE_RT_CTAS_PER_SM, VG_TUNE_MERGE_WORDS = 0, 1, 2, 3
+VG_TUNE_RT_LANES, VG_TUNE_INFLATE_TILE, VG_TUNE_RT_CTAS_PER_SM, VG_TUNE_MERGE_WORDS, VG_TUNE_INFLATE_TMA = range(5)
 VG_TILE_AUTO, VG_TILE_4x8x4, VG_TILE_4x8x8, VG_TILE_8x8x4, VG_TILE_8x8x8 = range(5)
 TILE_NAMES = {VG_TILE_AUTO: "auto", VG_TILE_4x8x4: "4x8x4", VG_TILE_4x8x8: "4x8x8", VG_TILE_8x8x4: "8x8x4",
               VG_TILE_8x8x8: "8x8x8"}
@@ -49,7 +49,8 @@ class vg_params(C.Structure):
 
 
 class vg_stats_t(C.Structure):
-    _fields_ = [("frames", C.c_uint64), ("points_in_grid", C.c_uint64), ("ray_visits", C.c_uint64)]
+    _fields_ = [("frames", C.c_uint64), ("points_in_grid", C.c_uint64), ("ray_visits", C.c_uint64),
+                ("wait_timeouts", C.c_uint64)]
 
 
 class vg_frame(C.Structure):
@@ -337,7 +338,8 @@ def vg_get_origin(h):
 def vg_stats(h):
     s = vg_stats_t()
     _check(load().vg_stats(h, C.byref(s)), "vg_stats")
-    return {"frames": s.frames, "points_in_grid": s.points_in_grid, "ray_visits": s.ray_visits}
+    return {"frames": s.frames, "points_in_grid": s.points_in_grid, "ray_visits": s.ray_visits,
+            "wait_timeouts": s.wait_timeouts}
 
 
 def vg_profile_enable(h, enable=True):
@@ -405,15 +407,16 @@ class Grid:
 
     def autotune(self, depth, T_wc, depth_scale=1.0, reps=5, stream=None):
         """Times the schedule knobs on this frame and keeps the fastest;
-        returns {"tile", "lanes", "ctas_per_sm", "merge_words"}."""
+        returns {"tile", "lanes", "ctas_per_sm", "merge_words", "inflate_tma"}."""
         ptr, mem, nbytes, dt = _buffer(depth)
         dtype = _depth_dtype(dt)
         H, W = depth.shape
         T, tp = _f64(T_wc, 16)
-        best = (C.c_int32 * 4)()
+        best = (C.c_int32 * 5)()
         _check(load().vg_autotune(self.h, ptr, mem, W, H, dtype, float(depth_scale), tp, int(reps), _stream(stream),
                                   best), "vg_autotune")
-        return {"tile": TILE_NAMES[best[0]], "lanes": best[1], "ctas_per_sm": best[2], "merge_words": best[3]}
+        return {"tile": TILE_NAMES[best[0]], "lanes": best[1], "ctas_per_sm": best[2], "merge_words": best[3],
+                "inflate_tma": best[4]}
 
     def close(self):
         if self.h:

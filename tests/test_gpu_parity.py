@@ -132,13 +132,15 @@ def test_hires_u16_full_size(vg):
 def test_schedule_knobs_keep_results(vg, tile, r):
     # every schedule the per-grid autotuner can pick: the four inflate tiles
     # at radii 1-3 (on a grid with 8-word rows, so 8-word tiles are used),
-    # K3 capped at few CTAs per SM, and K4's 512-word units with re-centres
+    # staged by tensor copies or by the threads, K3 capped at few CTAs per
+    # SM, and K4's 256- and 512-word units with re-centres
     w = make("robot", robot=90 + r, frames=3, spec=(640, 480, 0.05, (256, 120, 60), r))
     g = w.grid
     P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos)
     P.g.set(vg.VG_TUNE_INFLATE_TILE, tile)
     P.g.set(vg.VG_TUNE_RT_CTAS_PER_SM, tile)          # 1..4 CTAs per SM
     P.g.set(vg.VG_TUNE_MERGE_WORDS, 512 if tile % 2 else 256)
+    P.g.set(vg.VG_TUNE_INFLATE_TMA, 1 if r != 2 else 0)   # tensor-copy staging, and thread staging at r 2
     for f in w.frames:
         P.depth(f.depth, f.T_wc, check=False)
         P.check("tile %d r %d frame" % (tile, r))
