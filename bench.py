@@ -680,7 +680,9 @@ def run_ours(args):
         sched.update({vg.VG_TUNE_INFLATE_TILE: tiles[best["tile"]], vg.VG_TUNE_RT_LANES: best["lanes"],
                       vg.VG_TUNE_RT_CTAS_PER_SM: best["ctas_per_sm"], vg.VG_TUNE_MERGE_WORDS: best["merge_words"],
                       vg.VG_TUNE_INFLATE_TMA: best["inflate_tma"]})
-        tune_info = {"schedule": best}
+        tune_info = {"schedule": best,
+                     "schedule_is_default": (best["tile"] == "auto" and best["ctas_per_sm"] == 0 and
+                                             best["merge_words"] == 256 and best["inflate_tma"] == 1)}
 
     # warm-up steps, then about a second of pre-roll so clocks settle; the
     # timed steps continue on the same grid (its first frames pay one-time
@@ -721,7 +723,8 @@ def run_ours(args):
 
     if tune_info is not None:
         # the tuned and the default schedule over the same steps, frames
-        # alternating between a grid of each (so drifts hit both alike)
+        # alternating between a grid of each, in turn first (so drifts and
+        # the order hit both alike)
         gt, gd = new_grid(), new_grid(tuned=False)
         for k in range(3):   # untimed first frames of each grid
             step(gt, k)
@@ -729,10 +732,11 @@ def run_ours(args):
         ev2 = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
                for _ in range(2)]
         for k in range(args.steps):
-            for j, gr in enumerate((gt, gd)):
+            # the tuned grid first in even steps, the default one in odd ones
+            for j in ((0, 1) if k % 2 == 0 else (1, 0)):
                 flush.zero_()
                 ev2[j][k][0].record(stream)
-                step(gr, 3 + k)
+                step((gt, gd)[j], 3 + k)
                 ev2[j][k][1].record(stream)
         torch.cuda.synchronize()
         gt.close()

@@ -540,7 +540,8 @@ VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
  * words per CTA (256, 512) and K2's staging (tensor copies or threads) --
  * and compares each candidate value with the best schedule so far: `reps`
  * (1 .. 1000) measurements of the given depth frame (arguments as for
- * vg_integrate_depth) under each, alternating, every one starting with a
+ * vg_integrate_depth) under each, alternating and each in turn first,
+ * every one starting with a
  * cold L2 (a write of twice the L2's size to a scratch buffer the call
  * allocates and frees); the candidate wins only if its median CUDA event
  * time is at least 2 % below the incumbent's.  Keeps the winning schedule in the grid and writes
