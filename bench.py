@@ -929,6 +929,8 @@ def run_sweeps(args):
     set-up of Sec. V unless swept: 320x240, fov 85x101, depth 6.5 m,
     100x100x20 at 0.15 m, vox_inf 2."""
     import torch
+    from paper_2112_13169_gb300 import build as vgbuild
+    vgbuild.build()
     from paper_2112_13169_gb300 import vg
     from oracle import OracleParams
     from oracle import oracle as O
