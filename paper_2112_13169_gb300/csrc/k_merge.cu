@@ -19,8 +19,9 @@ __global__ void __launch_bounds__(256) k_merge_shift(const PlaneGeom g, Planes p
                                                      const int32_t dz) {
     __shared__ __align__(16) uint8_t sm[units::merge_shift_smem(WPU)];
     pdl_trigger();
-    pdl_wait();
-    units::merge_shift_unit<WPU, units::LoadRO, units::LoadPlain, RL>(g, pl, src, dst, dx, dy, dz, blockIdx.x, sm);
+    // the source grid is staged before the wait for K3 (see merge_shift_unit)
+    units::merge_shift_unit<WPU, units::LoadRO, units::LoadPlain, RL, true>(g, pl, src, dst, dx, dy, dz, blockIdx.x,
+                                                                            sm);
 }
 
 // The literal loc_grid reading of Alg. 2: the occupied voxels of loc_grid,

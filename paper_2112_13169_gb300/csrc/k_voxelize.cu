@@ -7,14 +7,16 @@ namespace {
 
 template <int DT, bool VEC>
 __global__ void __launch_bounds__(256) k_voxelize_depth(const FrameArgs a) {
-    pdl_trigger();
+    // K1 lets the frame's later kernels launch only once the work before
+    // the frame has completed: K4 stages the grid before it waits for K3
     pdl_wait();   // the depth image and the planes belong to earlier work
+    pdl_trigger();
     units::voxelize_depth_thread<DT, VEC>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_voxelize_points(const FrameArgs a) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     units::voxelize_points_thread(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 

@@ -28,7 +28,11 @@ namespace vg {
 // predecessor has completed and that kernel's writes are visible (pdl_wait).
 // Every such kernel waits in every CTA before it ends, so its completion
 // implies its predecessor's, and by induction all earlier work's.  Without
-// a programmatic predecessor both are no-ops.
+// a programmatic predecessor both are no-ops.  K1, the first kernel of a
+// frame, triggers only after its own wait: the frame's later kernels then
+// launch only once all work before the frame has completed, which lets K4
+// read the grid (written by the previous frame, not by K1-K3) before its
+// own wait.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

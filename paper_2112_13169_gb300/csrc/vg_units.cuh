@@ -400,7 +400,11 @@ __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl,
 __host__ __device__ constexpr int merge_shift_smem(int wpu) { return 2 * (32 * wpu + 32); }
 constexpr int kMergeShiftSmem = merge_shift_smem(256);
 
-template <int WPU, class LS, class LP, bool RAYS_LAST = false>
+// PDL_WAIT: the unit is a chained launch's only one (k_merge_shift); its
+// sources (the grid before this measurement, which K1-K3 do not write) are
+// staged before the launch waits for its predecessor (pdl_wait), so that
+// their DRAM latency overlaps the end of K3; the planes are read after it.
+template <int WPU, class LS, class LP, bool RAYS_LAST = false, bool PDL_WAIT = false>
 __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Planes &pl, const uint8_t *src,
                                                  uint8_t *dst, int32_t dx, int32_t dy, int32_t dz, int64_t u,
                                                  uint8_t *sm) {
@@ -425,7 +429,10 @@ __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Plane
         b0 = row * g.nx + min(xa, (int64_t)g.nx);
         b1 = row * g.nx + min(xa + kVox, (int64_t)g.nx);
     }
-    if (b0 >= b1) return;   // uniform over the CTA
+    if (b0 >= b1) {   // uniform over the CTA
+        if (PDL_WAIT) pdl_wait();
+        return;
+    }
     const int64_t off = (int64_t)dx + (int64_t)dy * g.nx + (int64_t)dz * g.nx * g.ny;
 
     // stage src[s0, s1): bytes [A, A + 16*n16) land at sm_src[0 ..); the
@@ -438,6 +445,7 @@ __device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Plane
         for (int i = tid; i < n16; i += 256)
             reinterpret_cast<uint4 *>(sm_src)[i] = LS::ld(reinterpret_cast<const uint4 *>(src + A) + i);
     }
+    if (PDL_WAIT) pdl_wait();
     __syncthreads();
 
     // results at sm_out[q0 + (i - b0)], q0 = b0 mod 16, so that sm_out and
