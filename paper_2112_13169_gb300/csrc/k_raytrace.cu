@@ -65,8 +65,8 @@ cudaError_t launch_lpr(const FrameArgs &a, int idx, cudaStream_t s, int ctas_per
     const int64_t resident = (int64_t)g_sms[dev] * per_sm;
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
     if (blocks == 0) return cudaSuccess;
-    // a packed visit holds a plane bit index below 2^31
-    const int buffered = a.g.words < (int64_t(1) << 26) ? 1 : 0;
+    // a packed run holds a plane bit index below 2^26
+    const int buffered = a.g.words < kRunWords ? 1 : 0;
     const size_t dyn = sizeof(uint32_t) * kRtBuf * kThreads;
     // traced marks must skip tested-occupied voxels only when the tested
     // plane is not covered by occ_inf (the literal loc_grid reading)

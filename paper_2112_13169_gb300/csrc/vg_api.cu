@@ -852,7 +852,7 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
         it.tiles[1] = (G->g.ny + 7) / 8;
         it.tiles[2] = (G->g.nz + it.tz - 1) / it.tz;
         it.align8 = (G->g.nx % 8 == 0 && reinterpret_cast<uintptr_t>(G->loc) % 8 == 0) ? 1 : 0;
-        it.buffered = G->g.words < (int64_t(1) << 26) ? 1 : 0;
+        it.buffered = G->g.words < vg::kRunWords ? 1 : 0;
         const int64_t npix = (int64_t)f.width * f.height;
         const int64_t nrays = (2 * (int64_t)G->hw + 1) * (2 * (int64_t)G->hh + 1);
         int64_t units[4] = {

@@ -52,9 +52,12 @@ cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
 }
 
 constexpr int kMaxInflate = 15;
-// In-grid visits a K3 lane keeps in shared memory.  36 entries (36 KB per
-// 256-thread CTA plus 6 KB of box) let five CTAs share an SM.
+// Entries (runs of in-grid visits) a K3 lane keeps in shared memory.  36
+// entries (36 KB per 256-thread CTA plus 6 KB of box) let five CTAs share an
+// SM.  A packed run needs plane bit indices below 2^26, i.e. plane words
+// below kRunWords; larger grids walk each slice twice instead.
 constexpr int kRtBuf = 36;
+constexpr int64_t kRunWords = int64_t(1) << 21;
 
 struct PlaneGeom {
     int32_t nx, ny, nz;
@@ -116,7 +119,7 @@ struct BatchItem {
     int32_t tz;         // inflate tile height in slices: 4 or 8
     int32_t mwpu;       // plane words per phase-4 unit of a merge with a re-centre: 256 or 512
     int32_t align8;     // loc rows and buffer allow 8-byte stores
-    int32_t buffered;   // packed visits fit (plane words < 2^26)
+    int32_t buffered;   // packed runs fit (plane words < kRunWords)
     int32_t dx, dy, dz; // pending re-centre of the grid, applied by the merge
     uint8_t *loc_dst;   // non-null: merge a.loc shifted by (dx, dy, dz) into loc_dst
 };

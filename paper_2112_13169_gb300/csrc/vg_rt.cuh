@@ -46,18 +46,19 @@
 // voxel and finish a slice in which the ray leaves the grid.
 //
 // Pass 1: each lane walks its slice once and keeps its in-grid visits in
-// its own shared-memory column (kRtBuf entries), then finds the first
-// occupied one, kChunk occupancy words in flight at a time.  A ballot over
-// the ray's lanes gives the first lane F that met one.
-// Pass 2: each lane replays its visits and marks: free before the ray's
+// its own shared-memory column (kRtBuf entries) as runs: consecutive visits
+// in one 32-voxel word, which can only be x-steps of one sign, share an
+// entry.  It then finds the first occupied visit, one occupancy word per
+// run and kChunk runs in flight at a time.  A ballot over the ray's lanes
+// gives the first lane F that met one.
+// Pass 2: each lane replays its runs and marks: free before the ray's
 // first occupied voxel, traced from it on (lanes before F all free, lanes
-// after F all traced).  Traced marks are written without re-reading the
-// occupancy: a traced mark on an occupied voxel, the first one included, is
-// overridden by K4.  Marks that fall in the same 32-voxel word are OR-ed in
-// a register and flushed with one atomicOr; near the camera, where all rays
-// overlap, they go to a per-CTA shared-memory box first (see kBoxW).
-// A lane whose slice holds more than kRtBuf in-grid visits, or a grid whose
-// planes are too large for a packed visit, walks twice instead.
+// after F all traced), one atomicOr per run and kind.  Traced marks are
+// written without re-reading the occupancy: a traced mark on an occupied
+// voxel, the first one included, is overridden by K4.  Near the camera,
+// where all rays overlap, marks go to a per-CTA shared-memory box first
+// (see kBoxW).  A lane whose slice holds more than kRtBuf runs, or a grid
+// whose planes are too large for a packed run, walks twice instead.
 //
 // Work mapping: warp w of group g takes a bundle of 32 / LPR neighbouring
 // rays, bundle w * G + g of the frame's G groups, so every group samples
@@ -85,6 +86,37 @@ constexpr int kBoxWords = kBoxW * kBoxY * kBoxZ;
 // else the plane bit index P = ((z*ny + y) * 32*wx + x) < 2^31; bits 0..4
 // are x & 31 either way, so p >> 5 is the word.
 constexpr uint32_t kBoxFlag = 0x80000000u;
+
+// A run of visits packed in 32 bits: its first visit, packed as above, with
+// the number of further visits (n - 1 <= 31) in bits 26..30, which a plane
+// visit leaves free when plane bit indices are below 2^26 (plane words
+// below kRunWords) and a box visit always.  The run's bits are lo, lo + sx,
+// ..., lo + (n - 1) sx of its word, lo = bits 0..4, sx the ray's x step.
+constexpr uint32_t kRunOne = 1u << 26;                  // one more visit
+constexpr uint32_t kRunKey = kBoxFlag | 0x03ffffe0u;    // the word, box flag included
+
+__device__ __forceinline__ uint32_t run_mask(uint32_t e, int32_t sx) {
+    const uint32_t n = ((e >> 26) & 31u) + 1u, lo = e & 31u;
+    return (0xffffffffu >> (32u - n)) << (sx < 0 ? lo + 1u - n : lo);
+}
+
+// The bits of a run's word that its walk visits before bit b.
+__device__ __forceinline__ uint32_t bits_before(uint32_t b, int32_t sx) {
+    return sx < 0 ? ~((2u << b) - 1u) : (1u << b) - 1u;
+}
+
+// Appends visit v to a lane's runs, without a branch: the pending run
+// `cur` (in slot `last` of the column) grows if v is in its word, else v
+// starts the next one in the next slot; the pending run is stored every
+// time.  False when the column is full.
+__device__ __forceinline__ bool run_add(uint32_t *col, int32_t &last, uint32_t &cur, uint32_t v) {
+    const bool same = ((v ^ cur) & kRunKey) == 0;
+    cur = same ? cur + kRunOne : v;
+    last += same ? 0 : 1;
+    if (last == kRtBuf) return false;
+    col[last * kThreads] = cur;
+    return true;
+}
 
 struct Box {
     int32_t bw0, by0, bz0;
@@ -515,9 +547,10 @@ __device__ __forceinline__ void fast_step(const Ray &r, float tm, float &t0, flo
     }
 }
 
-// Pass 1 of a lane: its in-grid visits in walk order into its buffer column
-// col[q * kThreads], box-packed while the walk is inside the camera box,
-// plane bit indices after that.  Returns false when the column overflows.
+// Pass 1 of a lane: its in-grid visits in walk order, as runs, into its
+// buffer column col[q * kThreads], box-packed while the walk is inside the
+// camera box, plane bit indices after that.  Returns false when the column
+// overflows.
 //
 // Exact steps (walker_next, with in-grid tests) lead to the first in-grid
 // voxel.  From there the walk runs without tests while its next crossing is
@@ -528,7 +561,8 @@ __device__ __forceinline__ void fast_step(const Ray &r, float tm, float &t0, flo
 // warp stays converged.  If the walk leaves the grid within the slice,
 // exact steps finish it.
 __device__ __forceinline__ bool walk_record(const Ray &r, const Lane &ln, const int32_t n0[3], bool visit_start,
-                                            const Box &b, uint32_t R, uint32_t *col, int32_t &nvis) {
+                                            const Box &b, uint32_t R, uint32_t *col, int32_t &nent,
+                                            int32_t &nvis) {
     const float c_hi = ln.c_hi;
     Walker w;
     walker_init(w, r, n0, R);
@@ -545,16 +579,20 @@ __device__ __forceinline__ bool walk_record(const Ray &r, const Lane &ln, const 
     bool inb = dw < kBoxW && dy < kBoxY && dz < kBoxZ;
     uint32_t Pb = kBoxFlag | (((dz * kBoxY + dy) * kBoxW + dw) << 5) | ((uint32_t)w.i0 & 31u);
     const float t_lim = fminf(c_hi, ln.t_out), t_b = ln.t_box;
+    uint32_t cur = inb ? Pb : P;   // the pending run, in slot `last`
+    int32_t last = 0;
+    col[0] = cur;
+    nvis = 1;
     float tm;
     for (;;) {
-        if (nvis == kRtBuf) return false;
-        col[nvis * kThreads] = inb ? Pb : P;
-        ++nvis;
         tm = fminf(t0, fminf(t1, t2));
         if (!(tm < t_lim)) break;
         inb = inb && tm < t_b;
         fast_step<true>(r, tm, t0, t1, t2, nb0, nb1, nb2, P, Pb);
+        if (!run_add(col, last, cur, inb ? Pb : P)) return false;
+        ++nvis;
     }
+    nent = last + 1;
     if (!(tm < c_hi)) return true;   // the next crossing is the next lane's
 
     // the walk leaves the grid within this slice: exact steps from here
@@ -571,95 +609,103 @@ __device__ __forceinline__ bool walk_record(const Ray &r, const Lane &ln, const 
     more = walker_next(w, r, c_hi);
     while (more) {
         if (in_grid(w, r)) {
-            if (nvis == kRtBuf) return false;
-            col[nvis * kThreads] = w.P;
+            if (!run_add(col, last, cur, w.P)) return false;
             ++nvis;
         } else if (gone(w, r)) {
             break;
         }
         more = walker_next(w, r, c_hi);
     }
+    nent = last + 1;
     return true;
 }
 
-// Index among the recorded visits of the first one the rays see occupied,
-// or -1; kChunk occupancy words in flight at a time (box visits read the
-// staged box).
+// Index of the first recorded run that holds a voxel the rays see
+// occupied, or -1, and in hit_bit that voxel's bit; kChunk occupancy words
+// in flight at a time (box runs read the staged box).
 template <class L>
 __device__ __forceinline__ int32_t first_hit(const FrameArgs &a, const uint32_t *occ_box, const uint32_t *col,
-                                             int32_t nvis) {
-    for (int32_t q0 = 0; q0 < nvis; q0 += kChunk) {
-        uint32_t p[kChunk], v[kChunk];
+                                             int32_t nent, int32_t sx, uint32_t &hit_bit) {
+    for (int32_t q0 = 0; q0 < nent; q0 += kChunk) {
+        uint32_t e[kChunk], v[kChunk];
 #pragma unroll
-        for (int c = 0; c < kChunk; ++c) p[c] = q0 + c < nvis ? col[(q0 + c) * kThreads] : 0u;
+        for (int c = 0; c < kChunk; ++c) e[c] = q0 + c < nent ? col[(q0 + c) * kThreads] : 0u;
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) {
             // both sources without a branch: the box word (any index is in
-            // range) and, for a plane visit, the plane word
-            const bool isb = (p[c] & kBoxFlag) != 0;
-            const uint32_t vb = occ_box[(p[c] >> 5) & (kBoxWords - 1)];
+            // range) and, for a plane run, the plane word
+            const bool isb = (e[c] & kBoxFlag) != 0;
+            const uint32_t vb = occ_box[(e[c] >> 5) & (kBoxWords - 1)];
             uint32_t vg = 0;
-            if (!isb && q0 + c < nvis) vg = L::ld(a.occ_test + (p[c] >> 5));
-            v[c] = isb ? vb : vg;
+            if (!isb && q0 + c < nent) vg = L::ld(a.occ_test + ((e[c] >> 5) & (uint32_t)(kRunWords - 1)));
+            v[c] = (isb ? vb : vg) & run_mask(e[c], sx);
         }
         int32_t hit = -1;
+        uint32_t h = 0;
 #pragma unroll
         for (int c = kChunk - 1; c >= 0; --c)
-            if (q0 + c < nvis && ((v[c] >> (p[c] & 31u)) & 1u)) hit = q0 + c;
-        if (hit >= 0) return hit;
+            if (q0 + c < nent && v[c]) {
+                hit = q0 + c;
+                h = v[c];
+            }
+        if (hit >= 0) {
+            hit_bit = sx < 0 ? 31u - (uint32_t)__clz(h) : (uint32_t)(__ffs(h) - 1);
+            return hit;
+        }
     }
     return -1;
 }
 
-// Marks the recorded visits: q < f_end free, the rest traced.  Runs of
-// visits of the same kind in the same 32-voxel word are OR-ed in a register
-// and written with one atomicOr, to the box arrays or the planes.  The key
-// of a run is the visit's word (p >> 5, which carries the box flag in bit
-// 26) with the kind in bit 31.
-__device__ __forceinline__ void mark_flush(const FrameArgs &a, uint32_t *box_fr, uint32_t *box_tr, uint32_t key,
-                                           uint32_t bits) {
-    if (!bits) return;
-    const bool traced = key >> 31;
-    if (key & (kBoxFlag >> 5)) atomicOr((traced ? box_tr : box_fr) + (key & (kBoxWords - 1)), bits);
-    else atomicOr((traced ? a.pl.tr : a.pl.fr) + (key & 0x03ffffffu), bits);
-}
-
-__device__ __forceinline__ void mark_visits(const FrameArgs &a, uint32_t *box_fr, uint32_t *box_tr,
-                                            const uint32_t *col, int32_t nvis, int32_t f_end) {
-    uint32_t key = 0xffffffffu, bits = 0;
-    for (int32_t q = 0; q < nvis; ++q) {
-        const uint32_t p = col[q * kThreads];
-        const uint32_t k = (p >> 5) | (q >= f_end ? 0x80000000u : 0u);
-        if (k != key) {
-            mark_flush(a, box_fr, box_tr, key, bits);
-            key = k;
-            bits = 0;
+// Marks the recorded runs: runs before f_q free, run f_q free before bit
+// f_bit (in walk order) and traced from it on, later runs traced.  One
+// atomicOr per run and kind, to the box arrays or the planes.  EXACT:
+// traced marks leave out voxels the rays test as occupied (see rt_resolve).
+template <bool EXACT, class L>
+__device__ __forceinline__ void mark_runs(const FrameArgs &a, uint32_t *box_fr, uint32_t *box_tr,
+                                          const uint32_t *occ_box, const uint32_t *col, int32_t nent, int32_t f_q,
+                                          uint32_t f_bit, int32_t sx) {
+    for (int32_t q = 0; q < nent; ++q) {
+        const uint32_t e = col[q * kThreads];
+        const uint32_t m = run_mask(e, sx);
+        uint32_t fr = q < f_q ? m : 0u;
+        if (q == f_q) fr = m & bits_before(f_bit, sx);
+        uint32_t tr = m & ~fr;
+        if (e & kBoxFlag) {
+            const uint32_t i = (e >> 5) & (kBoxWords - 1);
+            if (EXACT && tr) tr &= ~occ_box[i];
+            if (fr) atomicOr(box_fr + i, fr);
+            if (tr) atomicOr(box_tr + i, tr);
+        } else {
+            const uint32_t wi = (e >> 5) & (uint32_t)(kRunWords - 1);
+            if (EXACT && tr) tr &= ~L::ld(a.occ_test + wi);
+            if (fr) atomicOr(a.pl.fr + wi, fr);
+            if (tr) atomicOr(a.pl.tr + wi, tr);
         }
-        bits |= 1u << (p & 31u);
     }
-    mark_flush(a, box_fr, box_tr, key, bits);
 }
 
 // What pass 1 leaves for the rest of a lane's walk.
 struct Pass1 {
-    int32_t nvis;   // visits recorded in the lane's buffer column
+    int32_t nent;   // runs recorded in the lane's buffer column
+    int32_t nvis;   // visits they hold
     bool ovf;       // the slice does not fit the column: walk twice instead
 };
 
 // Pass 1 of a group's walk, by all threads of the CTA: each lane walks its
-// slice once and keeps its in-grid visits in its column of `buf` (box-packed
-// visits first, then plane bit indices).  Reads no global memory, so it may
+// slice once and keeps its in-grid visits in its column of `buf` as runs
+// (box-packed runs first, then plane bit indices).  Reads no global memory, so it may
 // run before the occupancy the visits are tested against is ready.
 // Warp-synchronous, like rt_walk.
 __device__ __forceinline__ Pass1 rt_record(const FrameArgs &a, const Lane &ln, const Box &b, int buffered,
                                            uint32_t *buf) {
-    Pass1 p1{0, !buffered};
+    Pass1 p1{0, 0, !buffered};
     const bool visit_start = ln.j == 0 && !(a.lit & kLitSkipStart);
     // (each phase starts with the warp reconverged, so that its lanes run
     // the phase's loop together rather than in groups)
     __syncwarp();
     if (ln.active && !p1.ovf)
-        p1.ovf = !walk_record(ln.r, ln, ln.n0, visit_start, b, 32u * (uint32_t)a.g.wx, buf + threadIdx.x, p1.nvis);
+        p1.ovf = !walk_record(ln.r, ln, ln.n0, visit_start, b, 32u * (uint32_t)a.g.wx, buf + threadIdx.x, p1.nent,
+                              p1.nvis);
     __syncwarp();
     return p1;
 }
@@ -686,14 +732,17 @@ __device__ __forceinline__ unsigned rt_resolve(const FrameArgs &a, const Lane &l
     const int32_t *n0 = ln.n0;
     const uint32_t R = 32u * (uint32_t)a.g.wx;
     const uint32_t *col = buf + threadIdx.x;
-    const int32_t nvis = p1.nvis;
+    const int32_t nent = p1.nent;
     const bool ovf = p1.ovf;
     const bool visit_start = j == 0 && !(a.lit & kLitSkipStart);
     unsigned visits = 0;
 
     // ---- first occupied visit of this lane -----------------------------
+    // (a run index with its bit for a buffered lane, a visit index for one
+    // that walks twice)
     int32_t hit_at = -1;
-    if (active && !ovf) hit_at = first_hit<L>(a, occ_box, col, nvis);
+    uint32_t hit_bit = 0;
+    if (active && !ovf) hit_at = first_hit<L>(a, occ_box, col, nent, r.s[0], hit_bit);
     if (active && ovf) hit_at = walk_first_hit<L>(a, r, n0, visit_start, c_hi, b, occ_box, R);
 
     // ---- first lane of this ray with an occupied voxel ---------------
@@ -705,22 +754,12 @@ __device__ __forceinline__ unsigned rt_resolve(const FrameArgs &a, const Lane &l
     const int mode = j < F ? 0 : (j == F ? 1 : 2);
 
     // ---- pass 2: mark free / traced -----------------------------------
-    if (!EXACT && active && !ovf) {
+    if (active && !ovf) {
         // free before the ray's first occupied voxel, traced from it on
         // (its own traced mark is overridden by K4: it is in occ_inf)
-        mark_visits(a, box_fr, box_tr, col, nvis, mode == 0 ? nvis : (mode == 1 ? hit_at : 0));
-        visits += (unsigned)nvis;
-    } else if (active && !ovf) {
-        Marks m;
-        for (int q = 0; q < nvis; ++q) {
-            if (mode == 1 && q == hit_at) continue;
-            const bool traced = mode == 2 || (mode == 1 && q > hit_at);
-            const uint32_t p = col[q * kThreads];
-            if (EXACT && traced && ((occ_word<L>(a, occ_box, p) >> (p & 31u)) & 1u)) continue;
-            marks_add(a, box_fr, box_tr, m, p, traced);
-        }
-        marks_flush(a, box_fr, box_tr, m);
-        visits += (unsigned)nvis;
+        mark_runs<EXACT, L>(a, box_fr, box_tr, occ_box, col, nent, mode == 0 ? nent : (mode == 1 ? hit_at : -1),
+                            hit_bit, r.s[0]);
+        visits += (unsigned)p1.nvis;
     } else if (active) {
         visits += walk_marks<EXACT, L>(a, r, n0, visit_start, c_hi, b, mode, hit_at, box_fr, box_tr, occ_box, R);
     }

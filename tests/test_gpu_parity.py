@@ -202,6 +202,19 @@ def test_huge_plane_takes_the_unbuffered_walk(vg):
     P.close()
 
 
+@pytest.mark.parametrize("ny", [511, 600])
+def test_plane_words_at_the_run_limit(vg, ny):
+    # 1 x 1024 x ny voxels at 4 words a row: 2,093,056 plane words (ny 511,
+    # just below 2^21: buffered runs, word indices up to bit 20) and
+    # 2,457,600 (ny 600: every lane walks twice)
+    rng = np.random.default_rng(31 + ny)
+    P = Pair(vg, (1, 1024, ny), 0.1, 87.0, 58.0, 1.5, 1, (0.0, 0.0, 0.0))
+    d = rng.uniform(0.2, 1.6, size=(24, 32)).astype(np.float32)
+    P.depth(d, body_pose([0.0, 0.0, 0.0], np.pi / 2))
+    P.depth(d, body_pose([0.0, 0.0, 0.0], -np.pi / 2, 0.2))
+    P.close()
+
+
 def test_host_memory_inputs(vg):
     run_workload(vg, make("room"), 1, device=False, shift=False)
 
