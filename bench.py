@@ -679,10 +679,11 @@ def run_ours(args):
         tiles = {v: k for k, v in vg.TILE_NAMES.items()}
         sched.update({vg.VG_TUNE_INFLATE_TILE: tiles[best["tile"]], vg.VG_TUNE_RT_LANES: best["lanes"],
                       vg.VG_TUNE_RT_CTAS_PER_SM: best["ctas_per_sm"], vg.VG_TUNE_MERGE_WORDS: best["merge_words"],
-                      vg.VG_TUNE_INFLATE_TMA: best["inflate_tma"]})
+                      vg.VG_TUNE_INFLATE_TMA: best["inflate_tma"], vg.VG_TUNE_EARLY_INFLATE: best["early_inflate"]})
         tune_info = {"schedule": best,
                      "schedule_is_default": (best["tile"] == "auto" and best["ctas_per_sm"] == 0 and
-                                             best["merge_words"] == 256 and best["inflate_tma"] == 1)}
+                                             best["merge_words"] == 256 and best["inflate_tma"] == 1 and
+                                             best["early_inflate"] == 1)}
 
     # warm-up steps, then about a second of pre-roll so clocks settle; the
     # timed steps continue on the same grid (its first frames pay one-time

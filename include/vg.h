@@ -521,6 +521,12 @@ VG_API int vg_profile_read(vg_grid *grid, double ms[VG_NKERNELS], int64_t timed[
  *                    1 (default): K2 moves each tile's raw words with one
  *                    tensor-memory-accelerator copy (radius 1..3); 0: its
  *                    threads load them.
+ *  VG_TUNE_EARLY_INFLATE
+ *                    1 (default): K2's CTAs launch while K1 runs, as soon
+ *                    as K1 has waited for the work before the frame; 0:
+ *                    they launch when K1 completes, which leaves K1's SM
+ *                    slots to K3's CTAs (their walk runs before they wait
+ *                    for K2).
  * Results do not depend on any of them.  Errors: VG_EINVAL.
  */
 enum {
@@ -528,7 +534,8 @@ enum {
     VG_TUNE_INFLATE_TILE = 1,
     VG_TUNE_RT_CTAS_PER_SM = 2,
     VG_TUNE_MERGE_WORDS = 3,
-    VG_TUNE_INFLATE_TMA = 4
+    VG_TUNE_INFLATE_TMA = 4,
+    VG_TUNE_EARLY_INFLATE = 5
 };
 enum { VG_TILE_AUTO = 0, VG_TILE_4x8x4 = 1, VG_TILE_4x8x8 = 2, VG_TILE_8x8x4 = 3, VG_TILE_8x8x8 = 4 };
 VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
@@ -537,7 +544,8 @@ VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
  * Autotuner of the per-frame kernels' schedule.  Starting from the grid's
  * schedule as it stands, it takes one knob at a time -- K2's tile (the four
  * shapes), K3's lanes per ray (8, 16, 32), K3's CTAs per SM (1..5), K4's
- * words per CTA (256, 512) and K2's staging (tensor copies or threads) --
+ * words per CTA (256, 512), K2's staging (tensor copies or threads) and
+ * K2's launch (while K1 runs or after it) --
  * and compares each candidate value with the best schedule so far: `reps`
  * (1 .. 1000) measurements of the given depth frame (arguments as for
  * vg_integrate_depth) under each, alternating and each in turn first,
@@ -545,7 +553,8 @@ VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
  * cold L2 (a write of twice the L2's size to a scratch buffer the call
  * allocates and frees); the candidate wins only if its median CUDA event
  * time is at least 2 % below the incumbent's.  Keeps the winning schedule in the grid and writes
- * it to best[5] = {tile, lanes, ctas_per_sm, merge_words, inflate_tma}
+ * it to best[6] = {tile, lanes, ctas_per_sm, merge_words, inflate_tma,
+ * early_inflate}
  * (tile VG_TILE_AUTO and ctas_per_sm 0 where the defaults won; may be
  * NULL).  Each timed measurement merges the frame over
  * a re-centre by zero, so K4 runs the re-centring merge that a moving
@@ -556,7 +565,7 @@ VG_API int vg_tune(vg_grid *grid, int32_t knob, int32_t value);
  */
 VG_API int vg_autotune(vg_grid *grid, const void *depth, int32_t mem, int32_t width, int32_t height,
                        int32_t dtype, float depth_scale, const double T_wc[16], int32_t reps, void *stream,
-                       int32_t best[5]);
+                       int32_t best[6]);
 
 /*
  * One measurement without any device allocation.  The paper has no

@@ -444,11 +444,16 @@ int vg_tune(vg_grid *G, int32_t knob, int32_t value) {
         G->sched.inflate_tma = value;
         return VG_OK;
     }
+    if (knob == VG_TUNE_EARLY_INFLATE) {
+        if (value != 0 && value != 1) return VG_EINVAL;
+        G->sched.early_inflate = value;
+        return VG_OK;
+    }
     return VG_EINVAL;
 }
 
 int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32_t height, int32_t dtype,
-                float depth_scale, const double T_wc[16], int32_t reps, void *stream, int32_t best[5]) {
+                float depth_scale, const double T_wc[16], int32_t reps, void *stream, int32_t best[6]) {
     if (!G || reps < 1 || reps > 1000) return VG_EINVAL;
     DeviceGuard dg(G->device);
     if (!dg.ok) return VG_ECUDA;
@@ -527,9 +532,10 @@ int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32
     const int ctas[5] = {1, 2, 3, 4, 5};
     const int words[2] = {256, 512};
     const int tma[2] = {1, 0};
+    const int early[2] = {1, 0};
     vg::Sched bs = G->sched;
     int bl = G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh);
-    for (int pass = 0; pass < 5 && rc == VG_OK; ++pass) {
+    for (int pass = 0; pass < 6 && rc == VG_OK; ++pass) {
         const int n = pass == 0 ? 4 : (pass == 1 ? 3 : (pass == 2 ? 5 : 2));
         if ((pass == 0 || pass == 4) && G->p.vox_inf == 0) continue;   // no K2 to tune
         for (int i = 0; i < n && rc == VG_OK; ++i) {
@@ -540,6 +546,7 @@ int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32
             if (pass == 2) sc.rt_ctas = ctas[i];
             if (pass == 3) sc.merge_words = words[i];
             if (pass == 4) sc.inflate_tma = tma[i];
+            if (pass == 5) sc.early_inflate = early[i];
             if (std::memcmp(&sc, &bs, sizeof(sc)) == 0 && lp == bl) continue;   // the incumbent itself
             bool win = false;
             rc = better(bs, bl, sc, lp, win);
@@ -561,6 +568,7 @@ int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32
         best[2] = bs.rt_ctas;
         best[3] = bs.merge_words;
         best[4] = bs.inflate_tma;
+        best[5] = bs.early_inflate;
     }
     return rc;
 }
@@ -584,7 +592,7 @@ int vg_integrate_depth(vg_grid *G, const void *depth, int32_t mem, int32_t width
         if (rc != VG_OK) return rc;
     }
     FrameArgs a = depth_frame_args(G, T, dptr, width, height, dtype, depth_scale);
-    cudaError_t e = launch(G, VG_K_VOXELIZE, s, [&] { return vg::launch_voxelize_depth(a, dtype, s); });
+    cudaError_t e = launch(G, VG_K_VOXELIZE, s, [&] { return vg::launch_voxelize_depth(a, dtype, s, G->sched); });
     if (e == cudaSuccess) e = finish_frame(G, a, s);
     if (e != cudaSuccess) return status_of(e);
     ++G->frames;
@@ -608,7 +616,7 @@ int vg_integrate_points(vg_grid *G, const float *xyz, int32_t mem, int64_t n, co
     FrameArgs a = frame_args(G, T);
     a.xyz = static_cast<const float *>(dptr);
     a.npts = n;
-    cudaError_t e = launch(G, VG_K_VOXELIZE, s, [&] { return vg::launch_voxelize_points(a, s); });
+    cudaError_t e = launch(G, VG_K_VOXELIZE, s, [&] { return vg::launch_voxelize_points(a, s, G->sched); });
     if (e == cudaSuccess) e = finish_frame(G, a, s);
     if (e != cudaSuccess) return status_of(e);
     ++G->frames;

@@ -163,11 +163,12 @@ struct Sched {
     int32_t rt_ctas = 0;        // K3 CTAs per SM; 0: as many as fit
     int32_t merge_words = 256;  // plane words per CTA of K4 with a re-centre: 256 or 512
     int32_t inflate_tma = 1;    // K2 stages its tiles with tensor-memory-accelerator copies (radius 1..3)
+    int32_t early_inflate = 1;  // K2 launches while K1 runs (else when K1 completes)
 };
 
 // Kernel launchers (one translation unit each).
-cudaError_t launch_voxelize_depth(const FrameArgs &a, int32_t dtype, cudaStream_t s);
-cudaError_t launch_voxelize_points(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_voxelize_depth(const FrameArgs &a, int32_t dtype, cudaStream_t s, const Sched &sc = Sched());
+cudaError_t launch_voxelize_points(const FrameArgs &a, cudaStream_t s, const Sched &sc = Sched());
 cudaError_t configure_inflate();   // once per device, before the first launch_inflate
 // device waits of K2 that ran out on the current device since the library was loaded
 cudaError_t wait_timeouts(unsigned *out);

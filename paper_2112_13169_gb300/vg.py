@@ -36,7 +36,8 @@ EXPORTS = ("vg_create", "vg_destroy", "vg_integrate_depth", "vg_integrate_points
 VG_TUNE_BATCH_CTAS_PER_SM, VG_TUNE_BATCH_LANES, VG_TUNE_BATCH_BARRIER_US, VG_TUNE_BATCH_BARRIER_EXTRA = 100, 101, 102, 103
 VG_TUNE_BATCH_INFLATE_SLICES, VG_TUNE_BATCH_MERGE_WORDS, VG_TUNE_BATCH_SPREAD = 104, 105, 106
 KERNELS = ("voxelize", "inflate", "raytrace", "merge", "shift", "loc_occupancy")
-VG_TUNE_RT_LANES, VG_TUNE_INFLATE_TILE, VG_TUNE_RT_CTAS_PER_SM, VG_TUNE_MERGE_WORDS, VG_TUNE_INFLATE_TMA = range(5)
+(VG_TUNE_RT_LANES, VG_TUNE_INFLATE_TILE, VG_TUNE_RT_CTAS_PER_SM, VG_TUNE_MERGE_WORDS, VG_TUNE_INFLATE_TMA,
+ VG_TUNE_EARLY_INFLATE) = range(6)
 VG_TILE_AUTO, VG_TILE_4x8x4, VG_TILE_4x8x8, VG_TILE_8x8x4, VG_TILE_8x8x8 = range(5)
 TILE_NAMES = {VG_TILE_AUTO: "auto", VG_TILE_4x8x4: "4x8x4", VG_TILE_4x8x8: "4x8x8", VG_TILE_8x8x4: "8x8x4",
               VG_TILE_8x8x8: "8x8x8"}
@@ -407,16 +408,16 @@ class Grid:
 
     def autotune(self, depth, T_wc, depth_scale=1.0, reps=5, stream=None):
         """Times the schedule knobs on this frame and keeps the fastest;
-        returns {"tile", "lanes", "ctas_per_sm", "merge_words", "inflate_tma"}."""
+        returns {"tile", "lanes", "ctas_per_sm", "merge_words", "inflate_tma", "early_inflate"}."""
         ptr, mem, nbytes, dt = _buffer(depth)
         dtype = _depth_dtype(dt)
         H, W = depth.shape
         T, tp = _f64(T_wc, 16)
-        best = (C.c_int32 * 5)()
+        best = (C.c_int32 * 6)()
         _check(load().vg_autotune(self.h, ptr, mem, W, H, dtype, float(depth_scale), tp, int(reps), _stream(stream),
                                   best), "vg_autotune")
         return {"tile": TILE_NAMES[best[0]], "lanes": best[1], "ctas_per_sm": best[2], "merge_words": best[3],
-                "inflate_tma": best[4]}
+                "inflate_tma": best[4], "early_inflate": best[5]}
 
     def close(self):
         if self.h:

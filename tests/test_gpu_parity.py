@@ -133,7 +133,8 @@ def test_schedule_knobs_keep_results(vg, tile, r):
     # every schedule the per-grid autotuner can pick: the four inflate tiles
     # at radii 1-3 (on a grid with 8-word rows, so 8-word tiles are used),
     # staged by tensor copies or by the threads, K3 capped at few CTAs per
-    # SM, and K4's 256- and 512-word units with re-centres
+    # SM, K4's 256- and 512-word units with re-centres, and K2 launched
+    # while K1 runs or after it
     w = make("robot", robot=90 + r, frames=3, spec=(640, 480, 0.05, (256, 120, 60), r))
     g = w.grid
     P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, w.frames[0].robot_pos)
@@ -141,6 +142,7 @@ def test_schedule_knobs_keep_results(vg, tile, r):
     P.g.set(vg.VG_TUNE_RT_CTAS_PER_SM, tile)          # 1..4 CTAs per SM
     P.g.set(vg.VG_TUNE_MERGE_WORDS, 512 if tile % 2 else 256)
     P.g.set(vg.VG_TUNE_INFLATE_TMA, 1 if r != 2 else 0)   # tensor-copy staging, and thread staging at r 2
+    P.g.set(vg.VG_TUNE_EARLY_INFLATE, tile % 2)
     for f in w.frames:
         P.depth(f.depth, f.T_wc, check=False)
         P.check("tile %d r %d frame" % (tile, r))
@@ -157,6 +159,7 @@ def test_autotune_picks_a_schedule_and_keeps_results(vg):
     best = P.g.autotune(d0, w.frames[0].T_wc, reps=2)
     assert best["tile"] in ("auto", "4x8x4", "4x8x8", "8x8x4", "8x8x8") and best["lanes"] in (8, 16, 32)
     assert 0 <= best["ctas_per_sm"] <= 5 and best["merge_words"] in (256, 512)
+    assert best["inflate_tma"] in (0, 1) and best["early_inflate"] in (0, 1)
     # the tuner merged frame 0 (over re-centres by zero); so does the oracle
     P.o.integrate_depth(w.frames[0].T_wc, w.frames[0].depth)
     P.check("after autotune")
