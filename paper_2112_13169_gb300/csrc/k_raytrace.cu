@@ -1,6 +1,6 @@
-// K3 as its own launch: persistent CTAs loop over groups of rays of one
-// frame, with the camera box staged once per CTA; the work itself is in
-// vg_rt.cuh.
+// K3 as its own launch: one resident wave of CTAs, each with one group of
+// rays of the frame and the camera box staged once; groups past the wave go
+// out bundle by bundle.  The work itself is in vg_rt.cuh.
 #include "vg_rt.cuh"
 
 namespace vg {
@@ -28,8 +28,25 @@ __global__ void __launch_bounds__(kThreads, 5) k_raytrace(const FrameArgs a, con
     pdl_wait();
     box_stage<units::LoadRO, false>(a, b, box_fr, box_tr, occ_box);
     unsigned visits = rt_resolve<LPR, units::LoadRO, EXACT>(a, ln, b, p1, box_fr, box_tr, occ_box, buf);
-    for (int64_t grp = blockIdx.x + gridDim.x; grp < groups; grp += gridDim.x)
-        visits += rt_group<LPR, units::LoadRO, EXACT>(a, S, b, grp, groups, buffered, box_fr, box_tr, occ_box, buf);
+    if (a.rt_next && groups > (int64_t)gridDim.x) {
+        // the groups past the launch's CTAs go out one bundle at a time, from
+        // a counter in device memory (zeroed by this frame's K1), so that the
+        // warps whose first bundles were short take more
+        constexpr int kWarps = kThreads / 32;
+        for (;;) {
+            uint32_t t = 0;
+            if ((threadIdx.x & 31) == 0) t = atomicAdd(a.rt_next, 1u);
+            t = __shfl_sync(kFull, t, 0);
+            const int64_t grp = (int64_t)gridDim.x + t / kWarps;
+            if (grp >= groups) break;
+            visits += rt_bundle<LPR, units::LoadRO, EXACT>(a, S, b, (int64_t)(t % kWarps) * groups + grp, buffered,
+                                                           box_fr, box_tr, occ_box, buf);
+        }
+    } else {
+        for (int64_t grp = blockIdx.x + gridDim.x; grp < groups; grp += gridDim.x)
+            visits += rt_group<LPR, units::LoadRO, EXACT>(a, S, b, grp, groups, buffered, box_fr, box_tr, occ_box,
+                                                          buf);
+    }
     box_flush(a, b, box_fr, box_tr);
     if (a.stats) {
         const unsigned total = __reduce_add_sync(kFull, visits);

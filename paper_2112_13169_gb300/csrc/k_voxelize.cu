@@ -14,12 +14,14 @@ template <int DT, bool VEC>
 __global__ void __launch_bounds__(256) k_voxelize_depth(const FrameArgs a, const int early) {
     pdl_wait();   // the depth image and the planes belong to earlier work
     if (early) pdl_trigger();
+    if (a.rt_next && blockIdx.x == 0 && threadIdx.x == 0) *a.rt_next = 0u;   // K3 of this frame counts from 0
     units::voxelize_depth_thread<DT, VEC>(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_voxelize_points(const FrameArgs a, const int early) {
     pdl_wait();
     if (early) pdl_trigger();
+    if (a.rt_next && blockIdx.x == 0 && threadIdx.x == 0) *a.rt_next = 0u;
     units::voxelize_points_thread(a, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 

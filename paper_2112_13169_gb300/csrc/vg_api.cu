@@ -216,6 +216,7 @@ FrameArgs frame_args(vg_grid *G, const vg::Pose32 &T) {
     a.pl = G->pl;
     a.loc = G->loc;
     a.stats = (G->p.flags & VG_FLAG_STATS) ? G->stats : nullptr;
+    a.rt_next = reinterpret_cast<uint32_t *>(G->stats + 31);   // the last 8 of the 256 stats bytes
     a.lit = ((G->p.flags & VG_FLAG_LIT_SKIP_START_VOXEL) ? vg::kLitSkipStart : 0) |
             ((G->p.flags & VG_FLAG_LIT_LOC_OCCUPANCY) ? vg::kLitRaysLast : 0);
     return a;

@@ -98,6 +98,7 @@ struct FrameArgs {
     Planes pl;
     uint8_t *loc;
     unsigned long long *stats;  // NULL unless VG_FLAG_STATS
+    uint32_t *rt_next;          // K3's counter of handed-out bundles, zeroed by K1; NULL: static only
     // literal readings (comparison flags; 0 for the default reading)
     const uint32_t *occ_test;   // the plane K3's rays test; NULL: pl.occ_inf
     int32_t lit;                // kLit* bits

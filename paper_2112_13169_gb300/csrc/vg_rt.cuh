@@ -404,24 +404,19 @@ __device__ __forceinline__ int64_t rt_groups(const FrameArgs &a) {
     return (nrays + kThreads / LPR - 1) / (kThreads / LPR);
 }
 
-// Set-up of this thread's lane for group `group` of the G >= rt_groups
-// groups the frame's rays are spread over.  Reads no memory but its
-// arguments.
+// Set-up of this thread's lane for bundle `bundle` of 32 / LPR neighbouring
+// rays (ray ids bundle * 32 / LPR ..), taken by this thread's warp; lanes
+// past the last ray are idle.  Reads no memory but its arguments.
 template <int LPR>
-__device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], const Box &bx, int64_t group,
-                                         int64_t G, Lane &ln) {
+__device__ __forceinline__ void rt_setup_bundle(const FrameArgs &a, const float S[3], const Box &bx, int64_t bundle,
+                                                Lane &ln) {
     const int lane = threadIdx.x & 31;
     const int j = lane & (LPR - 1);
     const int32_t width = 2 * a.hw + 1;
     const int64_t nrays = (int64_t)width * (2 * a.hh + 1);
     const uint32_t R = 32u * (uint32_t)a.g.wx;   // plane bits per row
-    // Warp w of group g takes bundle w * G + g of 32 / LPR neighbouring rays,
-    // so the warps of one group sample rows spread over the whole image and
-    // groups get similar amounts of work (rays of rows near the image's top
-    // and bottom leave the grid early).  Bundles past the last ray are idle;
-    // with G above the frame's own group count they spread evenly too.
     constexpr int kRaysPerWarp = 32 / LPR;
-    const int64_t ray = ((int64_t)(threadIdx.x >> 5) * G + group) * kRaysPerWarp + (lane / LPR);
+    const int64_t ray = bundle * kRaysPerWarp + (lane / LPR);
     ln.active = ray < nrays;
     ln.j = j;
     Ray &r = ln.r;
@@ -515,6 +510,18 @@ __device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], c
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) ln.n0[k] = j > 0 ? crossings_before(r, k, absD[k], c_lo) : 0;
+}
+
+// Set-up of this thread's lane for group `group` of the G >= rt_groups
+// groups the frame's rays are spread over.  Warp w of group g takes bundle
+// w * G + g, so the warps of one group sample rows spread over the whole
+// image and groups get similar amounts of work (rays of rows near the
+// image's top and bottom leave the grid early).  With G above the frame's
+// own group count the idle bundles spread evenly too.
+template <int LPR>
+__device__ __forceinline__ void rt_setup(const FrameArgs &a, const float S[3], const Box &bx, int64_t group,
+                                         int64_t G, Lane &ln) {
+    rt_setup_bundle<LPR>(a, S, bx, (int64_t)(threadIdx.x >> 5) * G + group, ln);
 }
 
 // One crossing of the fast walker (the caller has checked that tm, the
@@ -775,6 +782,16 @@ __device__ __forceinline__ unsigned rt_walk(const FrameArgs &a, const Lane &ln, 
                                             uint32_t *buf) {
     const Pass1 p1 = rt_record(a, ln, b, buffered, buf);
     return rt_resolve<LPR, L, EXACT>(a, ln, b, p1, box_fr, box_tr, occ_box, buf);
+}
+
+// One bundle of rays, by one warp: rt_setup_bundle then rt_walk.
+template <int LPR, class L, bool EXACT = false>
+__device__ __forceinline__ unsigned rt_bundle(const FrameArgs &a, const float S[3], const Box &b, int64_t bundle,
+                                              int buffered, uint32_t *box_fr, uint32_t *box_tr,
+                                              const uint32_t *occ_box, uint32_t *buf) {
+    Lane ln;
+    rt_setup_bundle<LPR>(a, S, b, bundle, ln);
+    return rt_walk<LPR, L, EXACT>(a, ln, b, buffered, box_fr, box_tr, occ_box, buf);
 }
 
 // One group of rays: rt_setup then rt_walk.
