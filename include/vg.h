@@ -316,10 +316,15 @@ VG_API int vg_batch_status(vg_batch *batch);
  *  VG_TUNE_BATCH_MERGE_WORDS  plane words per merge unit (phase 4) of a
  *                             grid whose merge applies a re-centre: 512 (the
  *                             default; 0 selects it) or 256.
- *  VG_TUNE_BATCH_SPREAD       1 (default): each frame's rays are spread over
- *                             proportionally more phase-3 units, so that the
- *                             CTAs' contiguous runs of units come out even;
- *                             0: one unit per group of 256 / LPR rays.
+ *  VG_TUNE_BATCH_SPREAD       how phase 3 (the ray trace) shares its units,
+ *                             groups of 256 / LPR rays, among the CTAs' contiguous
+ *                             runs.  2 (default): one unit per group; the runs
+ *                             split the units' total estimated cost evenly
+ *                             (each frame's unit cost from 25 of its rays'
+ *                             lengths in the grid).  1: each frame's rays are
+ *                             spread over proportionally more units, so that
+ *                             the runs hold equal numbers of units.  0: one
+ *                             unit per group, equal numbers of units.
  *  VG_TUNE_BATCH_BARRIER_US   how long a CTA of the fused launch waits at a
  *                             grid barrier before it gives up, in
  *                             microseconds, 1 .. 60,000,000, or 0 for the
@@ -353,7 +358,7 @@ VG_API int vg_batch_tune(vg_batch *batch, int32_t knob, int32_t value);
  * measurements into the grids, which leaves them as one step would) for
  * each candidate value of one schedule knob at a time -- CTAs per SM (1 ..
  * the occupancy limit), lanes per ray (per grid, 8, 16, 32), inflate tile
- * slices (8, 4), merge words per unit (512, 256), phase-3 spread (on, off)
+ * slices (8, 4), merge words per unit (512, 256), phase-3 spread (2, 1, 0)
  * -- with the other knobs at the best values found so far (coordinate
  * descent), keeps the fastest setting in the batch and writes it to best[5]
  * = {ctas_per_sm, lanes, inflate_slices, merge_words, spread} (may be NULL).

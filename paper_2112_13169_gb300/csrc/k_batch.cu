@@ -52,6 +52,22 @@ __device__ __forceinline__ int find_item(const BatchItem *items, int n, int phas
     return lo;
 }
 
+// The first phase-3 unit whose weighted start (woff3 + its index in its
+// frame x w3) is at least x, for 0 <= x <= ctl->wtotal3.
+__device__ __forceinline__ int64_t weighted_unit(const BatchItem *items, int n, int64_t total, int64_t x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {   // last item whose weighted offset is <= x
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&items[mid].woff3) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t first = __ldg(&items[lo].off[2]);
+    const int64_t units = (lo + 1 < n ? __ldg(&items[lo + 1].off[2]) : total) - first;
+    const int64_t w = __ldg(&items[lo].w3);
+    const int64_t k = (x - __ldg(&items[lo].woff3) + w - 1) / w;
+    return first + (k < units ? k : units);
+}
+
 // In the voxelize and ray-trace phases a CTA's units are a contiguous run
 // [lo, hi) of the phase's units, so that it moves to another frame (and
 // restages that frame's arguments) only a few times.  Their units cost about
@@ -163,9 +179,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
 
     // ---- phase 3: ray trace -----------------------------------------------
     // a contiguous run of units per CTA, so the camera box is staged again
-    // only when the run crosses into another frame
+    // only when the run crosses into another frame; the runs split the
+    // units' total weight evenly (weights of 1: their number)
     {
-        const int64_t lo = run_begin(ctl->total[2], blockIdx.x, nb), hi = run_begin(ctl->total[2], blockIdx.x + 1, nb);
+        const int64_t lo = weighted_unit(items, n, ctl->total[2], run_begin(ctl->wtotal3, blockIdx.x, nb));
+        const int64_t hi = weighted_unit(items, n, ctl->total[2], run_begin(ctl->wtotal3, blockIdx.x + 1, nb));
         int cur = -1, i = find_item(items, n, 2, lo);
         float S[3] = {0.0f, 0.0f, 0.0f};
         Box b = {0, 0, 0};

@@ -726,7 +726,7 @@ int vg_batch_create(int32_t capacity, vg_batch **out) {
     B->capacity = capacity;
     B->inflate_tz = 8;
     B->merge_words = vg::kBatchMergeWords;
-    B->spread = 1;
+    B->spread = 2;
     B->bar_ns = vg::kBarrierNs;
     B->bytes = sizeof(vg::BatchCtl) + (size_t)capacity * sizeof(vg::BatchItem);
     cudaError_t e = cudaGetDevice(&B->device);
@@ -778,7 +778,7 @@ int vg_batch_tune(vg_batch *B, int32_t knob, int32_t value) {
         return VG_OK;
     }
     if (knob == VG_TUNE_BATCH_SPREAD) {
-        if (value != 0 && value != 1) return VG_EINVAL;
+        if (value < 0 || value > 2) return VG_EINVAL;
         B->spread = value;
         return VG_OK;
     }
@@ -806,6 +806,32 @@ int batch_blocks(const vg_batch *B) {
     int blocks = max_blocks;
     if (B->ctas_per_sm > 0 && B->ctas_per_sm * sms < max_blocks) blocks = B->ctas_per_sm * sms;
     return blocks;
+}
+
+// The relative cost of one phase-3 unit of a frame (a group of 256 / lpr
+// rays): a lane's ray-trace work is its set-up, worth about five visits,
+// plus its share of a ray's in-grid visits.  The visits are estimated from
+// 5 x 5 of the bundle's rays: a ray from the camera S along D visits about
+// |D|_1 * t_end + 1 voxels, t_end the parameter (at most 1) where it leaves
+// the grid.  Scaled by 16 and clamped to [1, 4096].
+int64_t ray_unit_weight(const FrameArgs &a, int lpr) {
+    const float S[3] = {a.T.t[0] / a.vs, a.T.t[1] / a.vs, a.T.t[2] / a.vs};
+    const double n[3] = {(double)a.g.nx, (double)a.g.ny, (double)a.g.nz};
+    double sum = 0.0;
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            const double ra = a.hw * (i - 2) / 2.0, rb = a.hh * (j - 2) / 2.0;
+            double D[3], l1 = 0.0, t_end = 1.0;
+            for (int k = 0; k < 3; ++k) {
+                D[k] = a.T.R[3 * k] * ra + a.T.R[3 * k + 1] * rb + a.T.R[3 * k + 2] * (double)a.vd;
+                l1 += std::fabs(D[k]);
+                if (D[k] > 0.0) t_end = std::min(t_end, (n[k] - S[k]) / D[k]);
+                if (D[k] < 0.0) t_end = std::min(t_end, -S[k] / D[k]);
+            }
+            sum += l1 * std::max(t_end, 0.0) + 1.0;
+        }
+    const double w = 16.0 * (5.0 + sum / 25.0 / lpr);
+    return (int64_t)std::min(4096.0, std::max(1.0, std::round(w)));
 }
 
 }  // namespace
@@ -902,7 +928,7 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
     // than others, so each frame's rays are spread over proportionally more
     // (partly filled) units: G_i = ceil(groups_i * rounds * blocks / T)
     // (unless the spread is tuned off).
-    if (B->spread) {
+    if (B->spread == 1) {
         const int64_t T = total[2];
         const int64_t nb = batch_blocks(B);
         if (nb < 1) return VG_ECUDA;
@@ -915,8 +941,18 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
         }
         total[2] = off;
     }
+    // Phase 3's runs split the units' total weight evenly: with spread 2
+    // each frame's units weigh its estimated ray cost, otherwise 1 each.
+    int64_t wtotal = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int64_t units3 = (i + 1 < n ? items[i + 1].off[2] : total[2]) - items[i].off[2];
+        items[i].w3 = B->spread == 2 ? ray_unit_weight(items[i].a, items[i].lpr) : 1;
+        items[i].woff3 = wtotal;
+        wtotal += units3 * items[i].w3;
+    }
     std::memset(ctl, 0, sizeof(*ctl));
     ctl->n = n;
+    ctl->wtotal3 = wtotal;
     ctl->bar_ns = B->bar_ns;
     ctl->bar_extra = B->bar_extra;
     for (int p = 0; p < 4; ++p) ctl->total[p] = total[p];
@@ -994,7 +1030,7 @@ int vg_batch_autotune(vg_batch *B, const vg_frame *frames, int32_t n, int32_t re
     cand[1] = {0, 8, 16, 32};
     cand[2] = {8, 4};
     cand[3] = {512, 256};
-    cand[4] = {1, 0};
+    cand[4] = {2, 1, 0};
     auto apply = [&](const int v[5]) {
         B->ctas_per_sm = v[0];
         B->lanes = v[1];

@@ -123,6 +123,8 @@ struct BatchItem {
     int32_t buffered;   // packed runs fit (plane words < kRunWords)
     int32_t dx, dy, dz; // pending re-centre of the grid, applied by the merge
     uint8_t *loc_dst;   // non-null: merge a.loc shifted by (dx, dy, dz) into loc_dst
+    int64_t woff3;      // phase 3: weight of the units before this frame's
+    int64_t w3;         // phase 3: weight of each of this frame's units
 };
 
 // Plane words per phase-4 unit of a batch frame whose merge applies a
@@ -140,6 +142,7 @@ struct BatchCtl {
     unsigned error;     // set when a barrier wait ran out
     unsigned bar_extra; // arrivals a barrier waits for beyond the launch's CTAs (0; 1 only to test the time limit)
     int64_t bar_ns;     // how long a CTA waits at a grid barrier before giving up (globaltimer ns)
+    int64_t wtotal3;    // phase 3: the units' total weight, split evenly over the CTAs
 };
 
 // Default of BatchCtl::bar_ns: four seconds (a phase of any batch that fits
