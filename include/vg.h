@@ -507,8 +507,9 @@ VG_API int vg_profile_read(vg_grid *grid, double ms[VG_NKERNELS], int64_t timed[
  * Tuning knobs (defaults are set by vg_create):
  *  VG_TUNE_RT_LANES  lanes of a warp that share one ray in K3: 1, 2, 4, 8,
  *                    16 or 32, or 0 for automatic (the default: the fewest
- *                    lanes, at least 8, whose share of the longest ray fits
- *                    the per-lane visit buffer).  Results do not depend on it.
+ *                    lanes, at least 8, whose share of the longest ray is
+ *                    at most 1.5 times the per-lane buffer of runs of
+ *                    visits).  Results do not depend on it.
  *  VG_TUNE_INFLATE_TILE
  *                    K2's tile of plane words: VG_TILE_AUTO (the default:
  *                    8 words x 8 rows x 8 slices, 4 slices when the grid has
