@@ -467,6 +467,26 @@ def test_point_clouds_at_scale(vg, npts):
     P.close()
 
 
+def test_bundle_handout_restarts_every_frame(vg):
+    # with one K3 CTA per SM the paper's grid has more ray groups (260) than
+    # K3 has CTAs (152), so the rest go out one bundle at a time from the
+    # grid's counter, which each frame's K1 zeroes (the depth and the point
+    # kernel alike): every frame must still trace every ray
+    rng = np.random.default_rng(37)
+    P = Pair(vg, (100, 100, 20), 0.15, 85.0, 101.0, 6.5, 2, (7.5, 7.5, 1.4))
+    P.g.set(vg.VG_TUNE_RT_CTAS_PER_SM, 1)
+    for k in range(3):
+        pos = np.array([7.5 + 0.2 * k, 7.5 - 0.1 * k, 1.4])
+        z = rng.uniform(0.3, 6.5, 20000)
+        pts = np.stack([rng.uniform(-0.9, 0.9, 20000) * z, rng.uniform(-1.2, 1.2, 20000) * z, z], 1)
+        P.points(pts.astype(np.float32), body_pose(pos, 0.4 * k, 0.05))
+        d = rng.uniform(0.4, 6.3, size=(48, 64)).astype(np.float32)
+        d[rng.random(d.shape) < 0.1] = 0
+        P.depth(d, body_pose(pos, -0.3 * k, -0.05))
+        P.shift(pos + np.array([0.3, 0.0, 0.0]))
+    P.close()
+
+
 def test_read_write_roundtrip_and_resume(vg):
     rng = np.random.default_rng(19)
     P = _pair(vg, n=(40, 30, 16))
