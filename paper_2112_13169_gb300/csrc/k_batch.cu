@@ -7,11 +7,10 @@
 //                                  slices (radius 1..3)
 //   phase 3  K3 ray trace          groups of at most 256 / LPR rays (a
 //                                  frame's rays spread over its units)
-//   phase 4  K4 merge              256 plane words (512, or 256 if tuned,
-//                                  with a pending re-centre)
+//   phase 4  K4 merge              512 plane words (256 if tuned)
 // with a grid-wide barrier between phases.  A frame's re-centre (K5) is not
-// a phase: it is left pending on its grid and applied by that grid's next
-// merge, which then writes the whole grid out of place (merge_shift_unit).
+// a phase: it moves its grid's ring, and that grid's next merge sets the
+// voxels it brought in to unknown (Ring).
 // Units of every frame are laid end to end per phase (BatchItem::off).  A
 // CTA finds the frame of its first unit of a phase by binary search, steps
 // forward through the frames as its units advance (see run_begin), and runs
@@ -36,10 +35,6 @@ using namespace rt;
 constexpr int kInflateUnroll = 2;
 constexpr int kDynWords = kRtBuf * kThreads;   // also covers an inflate tile of radius <= 3
 static_assert(units::inflate_smem_words<3, 8, 8, 8>(3) <= (size_t)kDynWords, "inflate tile fits");
-// a merge with a pending re-centre takes units of kMergeWords plane words:
-// twice the one-step kernel's, so that each CTA keeps more loads in flight
-constexpr int kMergeWords = kBatchMergeWords;
-static_assert(units::merge_shift_smem(kMergeWords) <= 4 * kDynWords, "merge-with-shift staging fits");
 static_assert(sizeof(FrameArgs) % 4 == 0, "frame arguments copy as words");
 
 __device__ __forceinline__ int find_item(const BatchItem *items, int n, int phase, int64_t u) {
@@ -72,8 +67,8 @@ __device__ __forceinline__ int64_t weighted_unit(const BatchItem *items, int n, 
 // [lo, hi) of the phase's units, so that it moves to another frame (and
 // restages that frame's arguments) only a few times.  Their units cost about
 // the same in every frame.  The inflate and merge units cost more in some
-// frames than in others (tile width and radius; a merge with or without a
-// re-centre), so there the units go round the CTAs in turn.
+// frames than in others (tile width and radius; how much of a grid the
+// measurement marks), so there the units go round the CTAs in turn.
 __device__ __forceinline__ int64_t run_begin(int64_t total, unsigned b, unsigned nb) { return total * b / nb; }
 
 // The frame of unit u, given the frame i of an earlier unit of the same CTA
@@ -228,17 +223,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const BatchItem *__restri
         for (int64_t u = blockIdx.x; u < ctl->total[3]; u += nb) {
             i = next_item(items, n, 3, u, i);
             const BatchItem &it = items[i];
-            const int64_t w = (u - it.off[3]) * kThreads + threadIdx.x;
-            if (it.loc_dst && it.mwpu == 256)
-                units::merge_shift_unit<256, units::LoadL2, units::LoadL2>(
-                    it.a.g, it.a.pl, it.a.loc, it.loc_dst, it.dx, it.dy, it.dz, u - it.off[3],
-                    reinterpret_cast<uint8_t *>(dyn));
-            else if (it.loc_dst)
-                units::merge_shift_unit<kMergeWords, units::LoadL2, units::LoadL2>(
-                    it.a.g, it.a.pl, it.a.loc, it.loc_dst, it.dx, it.dy, it.dz, u - it.off[3],
-                    reinterpret_cast<uint8_t *>(dyn));
-            else if (it.align8) units::merge_word<true, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
-            else units::merge_word<false, units::LoadL2>(it.a.g, it.a.pl, it.a.loc, w);
+            // the unit's mwpu plane words, one or two per thread
+            for (int k = 0; k < it.mwpu; k += kThreads)
+                units::merge_word<units::LoadL2>(it.a.g, it.a.pl, it.a.loc, it.a.ring,
+                                                 (u - it.off[3]) * it.mwpu + k + threadIdx.x);
         }
     }
 }

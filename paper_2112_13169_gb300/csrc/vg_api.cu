@@ -31,12 +31,13 @@ struct vg_grid {
     vg::Sched sched;      // tile and launch shapes of K2..K4 (vg_tune, vg_autotune)
     int device;
     uint8_t *base;        // the one device allocation
-    uint8_t *loc;
-    uint8_t *loc_alt;
-    // A re-centre not yet applied to loc: the grid's content is loc shifted
-    // by pend (loc'[i] = loc[i + pend]); origin already holds o'.  The next
-    // merge applies it while it writes the grid out of place, so a frame
-    // followed by a re-centre costs one pass over loc instead of two.
+    uint8_t *loc;         // ring-addressed by ring (vg::Ring)
+    uint8_t *loc_alt;     // staging for reads into memory the device cannot store to
+    // A re-centre by d (o' = o + d) moves the ring by d at once; the voxels
+    // it brings in still hold stale bytes until the next merge sets them to
+    // unknown (a read treats them as unknown meanwhile): pend = d while that
+    // is pending.  origin already holds o'.
+    int32_t ring[3];
     bool pend_on;
     int32_t pend[3];
     vg::Planes pl;
@@ -247,16 +248,47 @@ cudaError_t launch(vg_grid *G, int kind, cudaStream_t s, F &&fn) {
     return cudaEventRecord(G->prof_ev[2 * i + 1], s);
 }
 
-// K2..K4 after K1 has filled occ_raw.
-// Applies a pending re-centre on its own (K5): loc shifted into loc_alt.
+// The grid's ring, with the voxels a pending re-centre by d brought in:
+// along each axis, x in [n - d, n) for d > 0, [0, -d) for d < 0, every x
+// for |d| >= n.
+vg::Ring ring_of(const vg_grid *G) {
+    vg::Ring R;
+    const int32_t n[3] = {G->g.nx, G->g.ny, G->g.nz};
+    for (int k = 0; k < 3; ++k) {
+        R.r[k] = G->ring[k];
+        const int64_t d = G->pend_on ? G->pend[k] : 0;
+        int64_t lo = 0, hi = 0;
+        if (d > 0) lo = std::max<int64_t>(0, n[k] - d), hi = n[k];
+        if (d < 0) lo = 0, hi = std::min<int64_t>(n[k], -d);
+        R.elo[k] = (int32_t)lo;
+        R.ehi[k] = (int32_t)hi;
+    }
+    return R;
+}
+
+// The ring moved by d: ((r + d) mod n) per axis.
+void move_ring(vg_grid *G, const int32_t d[3]) {
+    const int64_t n[3] = {G->g.nx, G->g.ny, G->g.nz};
+    for (int k = 0; k < 3; ++k) G->ring[k] = (int32_t)((((int64_t)G->ring[k] + d[k]) % n[k] + n[k]) % n[k]);
+}
+
+// Applies a pending re-centre on its own: K4 over the (empty, between
+// frames) planes sets the voxels it brought in to unknown.
 cudaError_t apply_pending(vg_grid *G, cudaStream_t s) {
     if (!G->pend_on) return cudaSuccess;
-    cudaError_t e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, G->pend, G->loc, G->loc_alt, s); });
+    FrameArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = G->g;
+    a.pl = G->pl;
+    a.loc = G->loc;
+    a.ring = ring_of(G);
+    cudaError_t e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_merge(a, s, G->sched); });
     if (e != cudaSuccess) return e;
-    std::swap(G->loc, G->loc_alt);
     G->pend_on = false;
     return cudaSuccess;
 }
+
+// K2..K4 after K1 has filled occ_raw.
 
 cudaError_t finish_frame(vg_grid *G, FrameArgs &a, cudaStream_t s) {
     cudaError_t e;
@@ -271,22 +303,21 @@ cudaError_t finish_frame(vg_grid *G, FrameArgs &a, cudaStream_t s) {
     a.occ_test = a.pl.occ_inf;
     if (G->p.flags & VG_FLAG_LIT_INFLATE_AFTER_TRACE) a.occ_test = a.pl.occ_raw;
     if (G->p.flags & VG_FLAG_LIT_LOC_OCCUPANCY) {
-        const int32_t none[3] = {0, 0, 0};
-        e = launch(G, VG_K_LOC_OCCUPANCY, s, [&] {
-            return vg::launch_loc_occupancy(G->g, G->loc, G->pend_on ? G->pend : none, G->loc_occ, s);
-        });
+        const vg::Ring R = ring_of(G);
+        e = launch(G, VG_K_LOC_OCCUPANCY, s,
+                   [&] { return vg::launch_loc_occupancy(G->g, G->loc, R, G->loc_occ, s); });
         if (e != cudaSuccess) return e;
         a.occ_test = G->loc_occ;
     }
     const int lpr = G->lanes_per_ray ? G->lanes_per_ray : vg::auto_lanes_per_ray(G->vd, G->hw, G->hh);
     e = launch(G, VG_K_RAYTRACE, s, [&] { return vg::launch_raytrace(a, lpr, s, G->sched); });
     if (e != cudaSuccess) return e;
-    if (!G->pend_on) return launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge(a, s); });
-    // the measurement is in the re-centred frame: merge it over the shifted
-    // grid, written whole into loc_alt
-    e = launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge_shift(a, G->pend, G->loc_alt, s, G->sched); });
+    // the measurement is in the grid's current frame: the merge writes it
+    // through the ring, and sets what a pending re-centre brought in (and
+    // the measurement does not mark) to unknown
+    a.ring = ring_of(G);
+    e = launch(G, VG_K_MERGE, s, [&] { return vg::launch_merge(a, s, G->sched); });
     if (e != cudaSuccess) return e;
-    std::swap(G->loc, G->loc_alt);
     G->pend_on = false;
     return cudaSuccess;
 }
@@ -460,9 +491,7 @@ int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32
     if (!dg.ok) return VG_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
     // a re-centre pending at the start is applied first, so that every timed
-    // frame starts from the same grid; each timed frame then merges with a
-    // re-centre by zero (the identity), so that K4 runs the re-centring
-    // merge as it does when the robot moves every frame
+    // frame starts from the same grid
     cudaError_t e = apply_pending(G, s);
     if (e != cudaSuccess) return status_of(e);
     // every timed frame starts with a cold L2: a write of twice its size
@@ -483,8 +512,6 @@ int vg_autotune(vg_grid *G, const void *depth, int32_t mem, int32_t width, int32
         G->lanes_per_ray = lp;
         if (cudaMemsetAsync(flush, 0, flush_bytes, s) != cudaSuccess) return VG_ECUDA;
         if (e0 && cudaEventRecord(e0, s) != cudaSuccess) return VG_ECUDA;
-        G->pend_on = true;
-        G->pend[0] = G->pend[1] = G->pend[2] = 0;
         const int c = vg_integrate_depth(G, depth, mem, width, height, dtype, depth_scale, T_wc, stream);
         if (c != VG_OK) return c;
         if (e1 && cudaEventRecord(e1, s) != cudaSuccess) return VG_ECUDA;
@@ -636,6 +663,7 @@ int vg_shift(vg_grid *G, const double robot_pos_w[3], void *stream) {
     // is unknown), so an earlier one is applied first
     cudaError_t e = apply_pending(G, (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
+    move_ring(G, delta);
     std::memcpy(G->pend, delta, sizeof(delta));
     G->pend_on = true;
     std::memcpy(G->origin, o2, sizeof(o2));
@@ -651,16 +679,18 @@ int vg_read(vg_grid *G, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes, int32_
     const cudaMemcpyKind kind = dst_mem == VG_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
-    if (G->pend_on) {
-        // the re-centred grid, without applying the re-centre: K5 writes it
-        // straight into dst where the device can store there (device memory
-        // or page-locked host memory, 16-byte aligned), else into loc_alt
-        // and then copies; the next merge still applies the re-centre
+    if (G->pend_on || G->ring[0] || G->ring[1] || G->ring[2]) {
+        // the grid in its own frame, out of the ring (voxels a pending
+        // re-centre brought in read as unknown; the grid is left as it is):
+        // K5 writes it straight into dst where the device can store there
+        // (device memory or page-locked host memory, 16-byte aligned), else
+        // into loc_alt and then copies
+        const vg::Ring R = ring_of(G);
         uint8_t *ddst = dst_mem == VG_MEM_DEVICE ? dst : static_cast<uint8_t *>(mapped_host(dst));
         if (ddst && reinterpret_cast<uintptr_t>(ddst) % 16 == 0) {
-            e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, G->pend, G->loc, ddst, s); });
+            e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, R, G->loc, ddst, s); });
         } else {
-            e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, G->pend, G->loc, G->loc_alt, s); });
+            e = launch(G, VG_K_SHIFT, s, [&] { return vg::launch_shift(G->g, R, G->loc, G->loc_alt, s); });
             if (e == cudaSuccess) e = cudaMemcpyAsync(dst, G->loc_alt, (size_t)G->g.nvox, kind, s);
         }
     } else {
@@ -688,7 +718,8 @@ int vg_write(vg_grid *G, const uint8_t *src, int32_t src_mem, int64_t src_bytes,
     if (e == cudaSuccess) e = cudaMemsetAsync(G->pl.fr, 0, (size_t)G->g.words * 4, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(G->pl.tr, 0, (size_t)G->g.words * 4, (cudaStream_t)stream);
     if (e != cudaSuccess) return status_of(e);
-    G->pend_on = false;   // replaced whole
+    G->pend_on = false;   // replaced whole, in the grid's own frame
+    G->ring[0] = G->ring[1] = G->ring[2] = 0;
     std::memcpy(G->origin, origin, sizeof(G->origin));
     return VG_OK;
 }
@@ -886,7 +917,6 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
         it.tiles[0] = (G->g.wx + it.txw - 1) / it.txw;
         it.tiles[1] = (G->g.ny + 7) / 8;
         it.tiles[2] = (G->g.nz + it.tz - 1) / it.tz;
-        it.align8 = (G->g.nx % 8 == 0 && reinterpret_cast<uintptr_t>(G->loc) % 8 == 0) ? 1 : 0;
         it.buffered = G->g.words < vg::kRunWords ? 1 : 0;
         const int64_t npix = (int64_t)f.width * f.height;
         const int64_t nrays = (2 * (int64_t)G->hw + 1) * (2 * (int64_t)G->hh + 1);
@@ -894,24 +924,19 @@ int vg_batch_prepare(vg_batch *B, const vg_frame *frames, int32_t n) {
             ((npix + 3) / 4 + 255) / 256,
             G->p.vox_inf > 0 ? (int64_t)it.tiles[0] * it.tiles[1] * it.tiles[2] : 0,
             (nrays + (256 / it.lpr) - 1) / (256 / it.lpr),
-            (G->g.words + 255) / 256};
-        if (G->pend_on) {
-            // the grid's pending re-centre is applied by this step's merge,
-            // which writes the grid whole into loc_alt
-            it.dx = G->pend[0];
-            it.dy = G->pend[1];
-            it.dz = G->pend[2];
-            it.loc_dst = G->loc_alt;
-            std::swap(G->loc, G->loc_alt);
-            G->pend_on = false;
-            units[3] = (G->g.words + it.mwpu - 1) / it.mwpu;
-        }
+            (G->g.words + it.mwpu - 1) / it.mwpu};
+        // the merge writes through the grid's ring and sets what a pending
+        // re-centre brought in to unknown
+        it.a.ring = ring_of(G);
+        G->pend_on = false;
         if (f.recentre) {
-            // left pending, for the grid's next merge (or read)
+            // the ring moves now; what the re-centre brings in is left
+            // pending, for the grid's next merge (or read)
             int32_t o2[3], d[3];
             origin_of(&G->p, f.robot_pos_w, o2);
             shift_delta(&G->p, G->origin, o2, d);
             if (d[0] || d[1] || d[2]) {
+                move_ring(G, d);
                 std::memcpy(G->pend, d, sizeof(d));
                 G->pend_on = true;
                 std::memcpy(G->origin, o2, sizeof(o2));

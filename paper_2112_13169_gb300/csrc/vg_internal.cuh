@@ -79,6 +79,19 @@ struct Planes {
     uint32_t *tr;
 };
 
+// Ring addressing of loc_grid.  Voxel (x, y, z) of the grid in its current
+// frame (origin o) is byte (z' * ny + y') * nx + x' of the buffer, with
+// x' = (x + r[0]) mod nx, y' = (y + r[1]) mod ny, z' = (z + r[2]) mod nz.
+// A re-centre by d (Sec. IV-E) moves r by d instead of moving the bytes;
+// the voxels it brings in (x in [elo[0], ehi[0]) or y in [elo[1], ehi[1])
+// or z in [elo[2], ehi[2]): those whose x + d (or y, z) lay outside the old
+// grid) still hold stale bytes, which the next K4 (or a read) turns into
+// unknown.  All zero: the buffer is the grid itself.
+struct Ring {
+    int32_t r[3];
+    int32_t elo[3], ehi[3];
+};
+
 struct FrameArgs {
     PlaneGeom g;
     Pose32 T;
@@ -97,6 +110,7 @@ struct FrameArgs {
     int32_t r;         // vox_inf
     Planes pl;
     uint8_t *loc;
+    Ring ring;                  // loc's ring addressing, with the voxels a re-centre brought in
     unsigned long long *stats;  // NULL unless VG_FLAG_STATS
     uint32_t *rt_next;          // K3's counter of handed-out bundles, zeroed by K1; NULL: static only
     // literal readings (comparison flags; 0 for the default reading)
@@ -118,11 +132,8 @@ struct BatchItem {
     int32_t lpr;        // K3 lanes per ray: 8, 16 or 32
     int32_t txw;        // inflate tile width in words: 4 or 8
     int32_t tz;         // inflate tile height in slices: 4 or 8
-    int32_t mwpu;       // plane words per phase-4 unit of a merge with a re-centre: 256 or 512
-    int32_t align8;     // loc rows and buffer allow 8-byte stores
+    int32_t mwpu;       // plane words per phase-4 unit: 256 or 512
     int32_t buffered;   // packed runs fit (plane words < kRunWords)
-    int32_t dx, dy, dz; // pending re-centre of the grid, applied by the merge
-    uint8_t *loc_dst;   // non-null: merge a.loc shifted by (dx, dy, dz) into loc_dst
     int64_t woff3;      // phase 3: weight of the units before this frame's
     int64_t w3;         // phase 3: weight of each of this frame's units
 };
@@ -165,7 +176,7 @@ enum {
 struct Sched {
     int32_t inflate_tile = kTileAuto;
     int32_t rt_ctas = 0;        // K3 CTAs per SM; 0: as many as fit
-    int32_t merge_words = 256;  // plane words per CTA of K4 with a re-centre: 256 or 512
+    int32_t merge_words = 256;  // plane words per CTA of K4: 256 (one per thread) or 512 (two)
     int32_t inflate_tma = 1;    // K2 stages its tiles with tensor-memory-accelerator copies (radius 1..3)
     int32_t early_inflate = 1;  // K2 launches while K1 runs (else when K1 completes)
 };
@@ -180,14 +191,13 @@ cudaError_t launch_inflate(const FrameArgs &a, cudaStream_t s, const Sched &sc =
 cudaError_t configure_raytrace(int dev);   // once per device, before the first launch_raytrace
 int auto_lanes_per_ray(int32_t vd, int32_t hw, int32_t hh);
 cudaError_t launch_raytrace(const FrameArgs &a, int lanes_per_ray, cudaStream_t s, const Sched &sc = Sched());
-cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s);
-// K4 over a pending re-centre: reads a.loc shifted by delta, writes every voxel of dst
-cudaError_t launch_merge_shift(const FrameArgs &a, const int32_t delta[3], uint8_t *dst, cudaStream_t s,
-                               const Sched &sc = Sched());
-cudaError_t launch_shift(const PlaneGeom &g, const int32_t delta[3], const uint8_t *src,
-                         uint8_t *dst, cudaStream_t s);
-// loc_grid's occupied voxels after a re-centre by delta, as a bit plane
-cudaError_t launch_loc_occupancy(const PlaneGeom &g, const uint8_t *loc, const int32_t delta[3], uint32_t *out,
+// K4 into the ring-addressed a.loc (a.ring), which also clears the voxels a
+// re-centre brought in; with all-zero planes only those
+cudaError_t launch_merge(const FrameArgs &a, cudaStream_t s, const Sched &sc = Sched());
+// K5: the grid in its own frame, out of the ring-addressed src (ring), into dst
+cudaError_t launch_shift(const PlaneGeom &g, const Ring &ring, const uint8_t *src, uint8_t *dst, cudaStream_t s);
+// loc_grid's occupied voxels in the grid's own frame, as a bit plane
+cudaError_t launch_loc_occupancy(const PlaneGeom &g, const uint8_t *loc, const Ring &ring, uint32_t *out,
                                  cudaStream_t s);
 cudaError_t configure_batch(int dev);   // once per device, before the first launch_batch
 int batch_max_blocks(int dev);          // CTAs of k_batch resident at once on the device

@@ -287,26 +287,20 @@ __device__ __forceinline__ void inflate_tile(const PlaneGeom &g, const uint32_t 
 // One 32-voxel plane word per thread.  The voxel's measurement state is
 // resolved from the three planes with precedence
 //   occupied (occ_inf) > free (fr) > unknown-and-traced (tr) > unknown,
-// and Alg. 3 writes it to loc_grid wherever it is not unknown.  A word with
-// no bit set in any plane touches neither loc_grid nor the planes, so the
-// pass reads the bit planes everywhere but loc_grid only inside the
-// measured frustum.  Loc bytes move as 8-byte words when the row layout and
-// the buffer allow.  Every plane word read non-zero is cleared, which
-// leaves all planes zero for the next frame (occ_raw is a subset of occ_inf,
-// so its non-zero words are cleared too).
+// and Alg. 3 writes it to loc_grid wherever it is not unknown.  loc_grid is
+// ring-addressed (Ring): a re-centre only moves the ring, and the voxels it
+// brings into the grid are set to unknown by the next merge.  A word with no
+// bit set in any plane and no voxel brought in touches neither loc_grid nor
+// the planes, so the pass reads the bit planes everywhere but writes
+// loc_grid only inside the measured frustum and the slabs a re-centre
+// brought in, and never reads it.  Every plane word read non-zero is
+// cleared, which leaves all planes zero for the next frame (occ_raw is a
+// subset of occ_inf, so its non-zero words are cleared too).
 // ---------------------------------------------------------------------------
 // RAYS_LAST: the literal loc_grid reading, in which the rays' marks replace
 // the measurement's occupied marks (free > traced > occupied).
-template <bool RAYS_LAST = false>
-__device__ __forceinline__ uint8_t resolve(uint32_t oc, uint32_t f, uint32_t t, int b, uint8_t old) {
-    if (!RAYS_LAST && ((oc >> b) & 1u)) return 2;   // VG_OCC
-    if ((f >> b) & 1u) return 1;                    // VG_FREE
-    if ((t >> b) & 1u) return 3;                    // VG_TRACED
-    if (RAYS_LAST && ((oc >> b) & 1u)) return 2;
-    return old;
-}
-
-// The same resolve for four voxels at once.  With the state codes
+//
+// The resolve works on four voxels at once.  With the state codes
 // OCC = 2, FREE = 1, TRACED = 3, a word's codes are two bit masks, hi (bit
 // 1 of each code: occupied or traced) and lo (bit 0: free or traced), and
 // known marks the voxels that are not unknown.  expand4 spreads a nibble
@@ -340,37 +334,91 @@ __device__ __forceinline__ uint32_t merge4(uint32_t hi, uint32_t lo, uint32_t kn
     return (old & ~(kb * 0xffu)) | code;
 }
 
-template <bool ALIGN8, class L, bool RAYS_LAST = false>
-__device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl, uint8_t *loc, int64_t w) {
+// The ring position of coordinate c (0 <= c < n) moved by r (0 <= r < n).
+__device__ __forceinline__ int32_t ring_at(int32_t c, int32_t r, int32_t n) {
+    const int32_t v = c + r;
+    return v >= n ? v - n : v;
+}
+
+// Bits of the voxels of a row word (x0 .. x0 + nbits - 1, row (y, z)) that a
+// re-centre brought into the grid: the whole word if its row did, else the
+// part of it inside [elo[0], ehi[0]).
+__device__ __forceinline__ uint32_t entering_bits(const Ring &R, int32_t x0, int32_t y, int32_t z, int nbits) {
+    const uint32_t all = nbits >= 32 ? 0xffffffffu : ((1u << nbits) - 1u);
+    if ((y >= R.elo[1] && y < R.ehi[1]) || (z >= R.elo[2] && z < R.ehi[2])) return all;
+    const int32_t lo = max(R.elo[0] - x0, 0), hi = min(R.ehi[0] - x0, nbits);
+    if (hi <= lo) return 0u;
+    const uint32_t below_hi = hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    return below_hi & ~((1u << lo) - 1u);
+}
+
+// Writes codes[v] (byte v of the 8 words codes[0..7], codes[8] = 0) to
+// p[v - v0] for the voxels v in [v0, v1) whose bit is set in touch: aligned
+// 4-byte stores where all four bytes are this word's and touched, byte
+// stores elsewhere, so that no store reaches a byte of another word.
+__device__ __forceinline__ void store_codes(uint8_t *p, int v0, int v1, const uint32_t codes[9], uint32_t touch) {
+    int v = v0;
+    // head: bytes up to the first 4-byte boundary of the buffer
+    while (v < v1 && (reinterpret_cast<uintptr_t>(p + (v - v0)) & 3u) != 0) {
+        if ((touch >> v) & 1u) p[v - v0] = (uint8_t)(codes[v >> 2] >> (8 * (v & 3)));
+        ++v;
+    }
+    for (; v + 4 <= v1; v += 4) {
+        const uint32_t t4 = (touch >> v) & 15u;
+        if (t4 == 0) continue;
+        const uint32_t w = __funnelshift_r(codes[v >> 2], codes[(v >> 2) + 1], 8 * (v & 3));
+        if (t4 == 15u) {
+            *reinterpret_cast<uint32_t *>(p + (v - v0)) = w;
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if ((t4 >> b) & 1u) p[v - v0 + b] = (uint8_t)(w >> (8 * b));
+        }
+    }
+    for (; v < v1; ++v)
+        if ((touch >> v) & 1u) p[v - v0] = (uint8_t)(codes[v >> 2] >> (8 * (v & 3)));
+}
+
+// K4 of one plane word w (the 32 voxels x0 .. x0 + 31 of one row of the
+// grid in its own frame) into the ring-addressed loc: the measurement's
+// codes where a plane marks a voxel, unknown where a re-centre brought the
+// voxel in and no plane marks it, nothing elsewhere.  loc is only written,
+// never read.  The row's voxels from x0 on sit at buffer x ring_at(x0, r[0])
+// up to the row's end, the rest (when the ring wraps inside the word) from
+// buffer x 0.  Clears the plane words it reads non-zero.
+template <class L, bool RAYS_LAST = false>
+__device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl, uint8_t *loc, const Ring &R,
+                                           int64_t w) {
     if (w >= g.words) return;
-    // rows are a power of two of words
+    // rows are a power of two of words; grids hold fewer than 2^31 voxels
     const int32_t wxi = (int32_t)(w & (g.wx - 1));
-    const int64_t row = w >> (__ffs(g.wx) - 1);
+    const uint32_t row = (uint32_t)(w >> (__ffs(g.wx) - 1));
     const int32_t x0 = wxi * 32;
     if (x0 >= g.nx) return;   // padding word, always zero
     const uint32_t oc = L::ld(pl.occ_inf + w), f = L::ld(pl.fr + w), t = L::ld(pl.tr + w);
     const uint32_t any = oc | f | t;
-    if (any == 0) return;
+    const int32_t y = (int32_t)(row % (uint32_t)g.ny), z = (int32_t)(row / (uint32_t)g.ny);
     const int nbits = min(32, g.nx - x0);
-    uint8_t *Lp = loc + row * g.nx + x0;
-    uint32_t hi, lo, known;
-    code_masks<RAYS_LAST>(oc, f, t, hi, lo, known);
+    const uint32_t ent = entering_bits(R, x0, y, z, nbits);
+    if ((any | ent) == 0) return;
+    uint32_t codes[9];
+    codes[8] = 0;
+    uint32_t touch = ent;
+    if (any) {
+        uint32_t hi, lo, known;
+        code_masks<RAYS_LAST>(oc, f, t, hi, lo, known);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        if (8 * c >= nbits) break;
-        const uint32_t m = (any >> (8 * c)) & 0xffu;
-        if (m == 0) continue;
-        if (ALIGN8 && 8 * c + 8 <= nbits) {
-            uint64_t *p = reinterpret_cast<uint64_t *>(Lp + 8 * c);
-            const uint64_t old = (m == 0xffu) ? 0ull : *p;
-            const uint32_t v0 = merge4(hi, lo, known, 2 * c, (uint32_t)old);
-            const uint32_t v1 = merge4(hi, lo, known, 2 * c + 1, (uint32_t)(old >> 32));
-            *p = ((uint64_t)v1 << 32) | v0;
-        } else {
-            for (int b = 8 * c; b < 8 * c + 8 && b < nbits; ++b)
-                if ((any >> b) & 1u) Lp[b] = resolve<RAYS_LAST>(oc, f, t, b, 0);
-        }
+        for (int m = 0; m < 8; ++m) codes[m] = merge4(hi, lo, known, m, 0u);
+        touch |= known;
+    } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) codes[m] = 0u;
     }
+    uint8_t *rowp = loc + ((int64_t)ring_at(z, R.r[2], g.nz) * g.ny + ring_at(y, R.r[1], g.ny)) * g.nx;
+    const int32_t xb = ring_at(x0, R.r[0], g.nx);
+    const int n1 = min(nbits, g.nx - xb);
+    store_codes(rowp + xb, 0, n1, codes, touch);
+    if (n1 < nbits) store_codes(rowp, n1, nbits, codes, touch);   // voxel v at rowp[v - n1]
     if (oc) {
         pl.occ_inf[w] = 0;
         pl.occ_raw[w] = 0;
@@ -379,208 +427,30 @@ __device__ __forceinline__ void merge_word(const PlaneGeom &g, const Planes &pl,
     if (t) pl.tr[w] = 0;
 }
 
-// K4 with a pending re-centre (Sec. IV-E followed by Alg. 3): unit u is the
-// WPU plane words u*WPU .. u*WPU+WPU-1 (WPU a multiple of 256), and writes
-// every voxel of the new grid they cover, dst[i] = the merge of the
-// measurement (whose planes are in the new grid's frame) over src[i + delta],
-// delta = dx + dy*Nx + dz*Nx*Ny, or over unknown where that voxel of the old
-// grid does not exist.  Clears the plane words it reads, as merge_word does.
-//
-// Because the plane row pitch wx is a power of two, the WPU words are whole
-// rows (wx <= WPU) or one part of a row (wx > WPU), so the unit's voxels are
-// one contiguous range [b0, b1) of at most 32*WPU bytes of dst, and their
-// sources one contiguous range of src.  The CTA stages the sources in shared
-// memory with aligned 16-byte loads (all issued before the first wait, so a
-// larger unit keeps more bytes in flight), each thread resolves the 32
-// voxels of each of its WPU/256 words into a second shared buffer, and the
-// results go out as aligned 16-byte stores.
-// sm: 16-byte aligned, merge_shift_smem(WPU) bytes.  Called by all threads
-// of a 256-thread CTA with the same u.  LS loads src (never written by the
-// launch), LP the planes (cleared by the launch).
-__host__ __device__ constexpr int merge_shift_smem(int wpu) { return 2 * (32 * wpu + 32); }
-constexpr int kMergeShiftSmem = merge_shift_smem(256);
-
-// PDL_WAIT: the unit is a chained launch's only one (k_merge_shift); its
-// sources (the grid before this measurement, which K1-K3 do not write) are
-// staged before the launch waits for its predecessor (pdl_wait), so that
-// their DRAM latency overlaps the end of K3; the planes are read after it.
-template <int WPU, class LS, class LP, bool RAYS_LAST = false, bool PDL_WAIT = false>
-__device__ __forceinline__ void merge_shift_unit(const PlaneGeom &g, const Planes &pl, const uint8_t *src,
-                                                 uint8_t *dst, int32_t dx, int32_t dy, int32_t dz, int64_t u,
-                                                 uint8_t *sm) {
-    static_assert(WPU % 256 == 0, "whole CTAs of words");
-    constexpr int kVox = 32 * WPU;
-    uint8_t *sm_src = sm;                 // staged sources, kVox + 16 bytes
-    uint8_t *sm_out = sm + kVox + 32;     // results, 16-byte aligned
-    const int tid = threadIdx.x;
-    const int64_t rows = (int64_t)g.ny * g.nz;
-    // rows are a power of two of words, and so is WPU; grids have fewer
-    // than 2^31 voxels, so rows and voxel indices fit 32 bits
-    const int lw = __ffs(g.wx) - 1;
-    int64_t b0, b1;
-    if (g.wx <= WPU) {
-        const int64_t R = WPU >> lw;
-        const int64_t r0 = u * R, r1 = min(r0 + R, rows);
-        b0 = r0 * g.nx;
-        b1 = r1 * g.nx;
-    } else {
-        const int lp = lw - (__ffs(WPU) - 1);   // log2 of the units per row
-        const int64_t row = u >> lp, xa = (u & ((int64_t(1) << lp) - 1)) * kVox;
-        b0 = row * g.nx + min(xa, (int64_t)g.nx);
-        b1 = row * g.nx + min(xa + kVox, (int64_t)g.nx);
-    }
-    if (b0 >= b1) {   // uniform over the CTA
-        if (PDL_WAIT) pdl_wait();
-        return;
-    }
-    const int64_t off = (int64_t)dx + (int64_t)dy * g.nx + (int64_t)dz * g.nx * g.ny;
-
-    // stage src[s0, s1): bytes [A, A + 16*n16) land at sm_src[0 ..); the
-    // last chunk may reach 15 bytes past nvox, into the buffer's slack
-    const int64_t s0 = max(b0 + off, (int64_t)0), s1 = min(b1 + off, g.nvox);
-    const int64_t A = s0 & ~int64_t(15);
-    __syncthreads();   // sm may still be read by the CTA's previous unit
-    if (s0 < s1) {
-        const int n16 = (int)((s1 - A + 15) >> 4);
-        for (int i = tid; i < n16; i += 256)
-            reinterpret_cast<uint4 *>(sm_src)[i] = LS::ld(reinterpret_cast<const uint4 *>(src + A) + i);
-    }
-    if (PDL_WAIT) pdl_wait();
-    __syncthreads();
-
-    // results at sm_out[q0 + (i - b0)], q0 = b0 mod 16, so that sm_out and
-    // dst agree on 16-byte alignment
-    const int q0 = (int)(b0 & 15);
-#pragma unroll 1
-    for (int k = 0; k < WPU / 256; ++k) {
-        // this thread's plane word and its 32 voxels
-        const int64_t w = u * WPU + k * 256 + tid;
-        const int32_t x0 = (int32_t)(w & (g.wx - 1)) * 32;
-        if (!(w < g.words && x0 < g.nx)) continue;
-        const uint32_t row = (uint32_t)(w >> lw);
-        const int32_t y = (int32_t)(row % (uint32_t)g.ny), z = (int32_t)(row / (uint32_t)g.ny);
-        const int nbits = min(32, g.nx - x0);
-        const int64_t d = (int64_t)row * g.nx + x0;
-        const uint32_t oc = LP::ld(pl.occ_inf + w), f = LP::ld(pl.fr + w), t = LP::ld(pl.tr + w);
-        const int32_t sy = y + dy, sz = z + dz, sx0 = x0 + dx;
-        const bool row_ok = (unsigned)sy < (unsigned)g.ny && (unsigned)sz < (unsigned)g.nz;
-        const int p = (int)(d + off - A);   // sm_src index of the first source voxel
-        uint32_t old[8];
-        if (row_ok && sx0 >= 0 && sx0 + nbits <= g.nx) {
-            // all present: aligned shared words and a funnel shift (bytes
-            // past nbits are garbage and discarded)
-            const uint32_t *ws = reinterpret_cast<const uint32_t *>(sm_src + (p & ~3));
-            const int sh = (p & 3) * 8;
-            uint32_t wv[9];
-#pragma unroll
-            for (int m = 0; m < 9; ++m) wv[m] = ws[m];
-#pragma unroll
-            for (int m = 0; m < 8; ++m) old[m] = __funnelshift_r(wv[m], wv[m + 1], sh);
-        } else {
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                uint32_t v = 0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int kk = 4 * m + b;
-                    if (row_ok && kk < nbits && (unsigned)(sx0 + kk) < (unsigned)g.nx)
-                        v |= (uint32_t)sm_src[p + kk] << (8 * b);
-                }
-                old[m] = v;
-            }
-        }
-        uint32_t nv[8];
-        if ((oc | f | t) == 0) {
-#pragma unroll
-            for (int m = 0; m < 8; ++m) nv[m] = old[m];
-        } else {
-            uint32_t hi, lo, known;
-            code_masks<RAYS_LAST>(oc, f, t, hi, lo, known);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) nv[m] = merge4(hi, lo, known, m, old[m]);
-            if (oc) {
-                pl.occ_inf[w] = 0;
-                pl.occ_raw[w] = 0;
-            }
-            if (f) pl.fr[w] = 0;
-            if (t) pl.tr[w] = 0;
-        }
-        const int q = q0 + (int)(d - b0);
-        const bool words = (q & 3) == 0;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            if (words && 4 * m + 4 <= nbits) {
-                *reinterpret_cast<uint32_t *>(sm_out + q + 4 * m) = nv[m];
-            } else {
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    if (4 * m + b < nbits) sm_out[q + 4 * m + b] = (uint8_t)(nv[m] >> (8 * b));
-            }
-        }
-    }
-    __syncthreads();
-    // [b0, h) and [t1, b1) bytewise, [h, t1) in aligned 16-byte chunks
-    const int64_t h = min(b1, (b0 + 15) & ~int64_t(15));
-    const int64_t t1 = max(h, b1 & ~int64_t(15));
-    const int64_t base = b0 - q0;   // dst address of sm_out[0]; a multiple of 16
-    if (tid < 16) {
-        const int64_t i = b0 + tid;
-        if (i < h) dst[i] = sm_out[i - base];
-    } else if (tid < 32) {
-        const int64_t i = t1 + (tid - 16);
-        if (i < b1) dst[i] = sm_out[i - base];
-    }
-    const int n16o = (int)((t1 - h) >> 4);
-    for (int i = tid; i < n16o; i += 256) {
-        const int64_t at = h + 16 * (int64_t)i;
-        *reinterpret_cast<uint4 *>(dst + at) = *reinterpret_cast<const uint4 *>(sm_out + (at - base));
-    }
-}
-
-// Units of merge_shift_unit<WPU> for a grid.
-template <int WPU>
-__host__ __device__ __forceinline__ int64_t merge_shift_units(const PlaneGeom &g) {
-    return (g.words + WPU - 1) / WPU;
-}
-
 // ---------------------------------------------------------------------------
-// K5: shift loc_grid to re-centre it on the robot (Sec. IV-E).
-//
-// An out-of-place copy with a constant flat offset: voxel (x, y, z) of the
-// new grid is voxel (x+dx, y+dy, z+dz) of the old one, i.e. flat index
-// i + dx + dy*Nx + dz*Nx*Ny, or unknown when that voxel does not exist.
-// One 16-byte chunk of the new grid per call.
+// K5: loc_grid in its own frame (Sec. IV-E), out of the ring-addressed
+// buffer: voxel (x, y, z) is the buffer's byte at the ring position of
+// (x, y, z), or unknown where a re-centre brought the voxel in.  One
+// 16-byte chunk of the output per call; dst is 16-byte aligned.
 // ---------------------------------------------------------------------------
 template <class L>
-__device__ __forceinline__ void shift_chunk(const PlaneGeom &g, int32_t dx, int32_t dy, int32_t dz,
-                                            const uint8_t *src, uint8_t *dst, int64_t chunk) {
+__device__ __forceinline__ void shift_chunk(const PlaneGeom &g, const Ring &R, const uint8_t *src, uint8_t *dst,
+                                            int64_t chunk) {
     const int64_t i0 = chunk * 16;
     if (i0 >= g.nvox) return;
-    const int64_t off = (int64_t)dx + (int64_t)dy * g.nx + (int64_t)dz * g.nx * g.ny;
     // grids hold fewer than 2^31 voxels: 32-bit division
     const uint32_t yz = (uint32_t)i0 / (uint32_t)g.nx;
     int32_t x = (int32_t)((uint32_t)i0 - yz * (uint32_t)g.nx);
     int32_t y = (int32_t)(yz % (uint32_t)g.ny), z = (int32_t)(yz / (uint32_t)g.ny);
-    // which of the 16 voxels have a source voxel
-    uint32_t valid = 0;
-#pragma unroll
-    for (int b = 0; b < 16; ++b) {
-        const int32_t sx = x + dx, sy = y + dy, sz = z + dz;
-        if (i0 + b < g.nvox && (unsigned)sx < (unsigned)g.nx && (unsigned)sy < (unsigned)g.ny &&
-            (unsigned)sz < (unsigned)g.nz)
-            valid |= 1u << b;
-        if (++x == g.nx) {
-            x = 0;
-            if (++y == g.ny) { y = 0; ++z; }
-        }
-    }
     uint32_t o[4];
-    if (valid == 0xffffu) {
-        // all sources exist: bytes [sb, sb+16) of src, 0 <= sb and sb+15 < nvox,
-        // read as five aligned words; the last may reach up to 4 bytes past
-        // nvox, into the slack the host leaves after every loc buffer, and
-        // those bytes are shifted out
-        const int64_t sb = i0 + off;
+    const int32_t xb = ring_at(x, R.r[0], g.nx);
+    const bool row_in = !((y >= R.elo[1] && y < R.ehi[1]) || (z >= R.elo[2] && z < R.ehi[2]));
+    if (i0 + 16 <= g.nvox && x + 16 <= g.nx && xb + 16 <= g.nx && row_in && (x + 16 <= R.elo[0] || x >= R.ehi[0])) {
+        // 16 voxels of one row, all old, contiguous in the buffer: bytes
+        // [sb, sb + 16), read as five aligned words; the last may reach up
+        // to 3 bytes past nvox, into the slack the host leaves after every
+        // loc buffer, and those bytes are shifted out
+        const int64_t sb = ((int64_t)ring_at(z, R.r[2], g.nz) * g.ny + ring_at(y, R.r[1], g.ny)) * g.nx + xb;
         const uint32_t *wsrc = reinterpret_cast<const uint32_t *>(src + (sb & ~int64_t(3)));
         const int sh = (int)(sb & 3) * 8;
         uint32_t wv[5];
@@ -591,7 +461,20 @@ __device__ __forceinline__ void shift_chunk(const PlaneGeom &g, int32_t dx, int3
     } else {
         uint8_t ob[16];
 #pragma unroll
-        for (int b = 0; b < 16; ++b) ob[b] = ((valid >> b) & 1u) ? L::ld(src + i0 + b + off) : (uint8_t)0;
+        for (int b = 0; b < 16; ++b) {
+            ob[b] = 0;
+            if (i0 + b < g.nvox) {
+                const bool in = !((x >= R.elo[0] && x < R.ehi[0]) || (y >= R.elo[1] && y < R.ehi[1]) ||
+                                  (z >= R.elo[2] && z < R.ehi[2]));
+                if (in)
+                    ob[b] = L::ld(src + ((int64_t)ring_at(z, R.r[2], g.nz) * g.ny + ring_at(y, R.r[1], g.ny)) * g.nx +
+                                  ring_at(x, R.r[0], g.nx));
+            }
+            if (++x == g.nx) {
+                x = 0;
+                if (++y == g.ny) { y = 0; ++z; }
+            }
+        }
 #pragma unroll
         for (int m = 0; m < 4; ++m)
             o[m] = ob[4 * m] | (ob[4 * m + 1] << 8) | (ob[4 * m + 2] << 16) | ((uint32_t)ob[4 * m + 3] << 24);
