@@ -467,6 +467,23 @@ def test_point_clouds_at_scale(vg, npts):
     P.close()
 
 
+@pytest.mark.parametrize("words", [256, 512])
+def test_rows_longer_than_a_merge_unit(vg, words):
+    # 16,400 voxels a row: 513 plane words, padded to 1024, so a 256- or
+    # 512-word K4 unit is one part of a row, and re-centres along x wrap the
+    # ring inside the parts
+    rng = np.random.default_rng(43 + words)
+    P = Pair(vg, (16400, 6, 4), 0.05, 87.0, 58.0, 2.0, 1, (0.0, 0.0, 0.0))
+    P.g.set(vg.VG_TUNE_MERGE_WORDS, words)
+    pos = np.array([0.0, 0.0, 0.0])
+    for k in range(4):
+        d = rng.uniform(0.3, 2.2, size=(24, 32)).astype(np.float32)
+        P.depth(d, body_pose(pos, 0.05 * k, 0.0))
+        pos = pos + np.array([0.37 * (k + 1), 0.0, 0.0])
+        P.shift(pos)
+    P.close()
+
+
 def test_bundle_handout_restarts_every_frame(vg):
     # with one K3 CTA per SM the paper's grid has more ray groups (260) than
     # K3 has CTAs (152), so the rest go out one bundle at a time from the
