@@ -188,10 +188,12 @@ VG_API int vg_integrate_points(vg_grid *grid, const float *xyz, int32_t mem, int
 /*
  * Re-centre the grid on the robot (Sec. IV-E): the new origin o' is computed
  * as in vg_create; with delta = o' - o, loc'[i] = loc[i + delta] where that
- * voxel exists, else VG_UNK.  The origin changes at once (vg_get_origin);
- * the copy of loc is deferred: the grid's next merge (vg_integrate_*, or a
- * batch step) writes the re-centred grid whole as it merges, and vg_read or
- * another vg_shift first applies a deferred re-centre on its own stream.
+ * voxel exists, else VG_UNK.  The origin changes at once (vg_get_origin).
+ * The grid is kept ring-addressed on the device, so no byte moves: the
+ * re-centre moves the ring, and the voxels it brings in (those whose
+ * loc[i + delta] does not exist) are set to VG_UNK by the grid's next merge
+ * (vg_integrate_*, or a batch step); vg_read returns them as VG_UNK
+ * meanwhile, and another vg_shift first clears them on its own stream.
  * No device work here unless a re-centre was already pending.
  * Errors: VG_EINVAL (also: |robot_pos_w| / vox_size >= 2^30 on an axis),
  * VG_ECUDA.
@@ -206,11 +208,12 @@ VG_API int vg_shift(vg_grid *grid, const double robot_pos_w[3], void *stream);
  * dst is valid once that work completes.  dst_mem is VG_MEM_DEVICE or
  * VG_MEM_HOST; dst_bytes must be >= Nx*Ny*Nz.  origin (may be NULL)
  * receives the grid origin (voxel index of voxel (0,0,0) in the world
- * lattice) as of this call.  With a re-centre pending (vg_shift), dst
- * receives the re-centred grid: K5 writes it on stream straight into dst
- * when dst is device memory or page-locked host memory and 16-byte aligned,
- * else through the grid's second buffer and a copy.  The grid's own state
- * does not change (the next merge still applies the re-centre).
+ * lattice) as of this call, in the layout above, re-centres included.  Once
+ * the grid has been re-centred, K5 reads it out of the device's ring
+ * addressing on stream, straight into dst when dst is device memory or
+ * page-locked host memory and 16-byte aligned, else through the grid's
+ * second buffer and a copy; before that, a plain copy.  The grid's own
+ * state does not change.
  * Errors: VG_EINVAL, VG_ECUDA.
  */
 VG_API int vg_read(vg_grid *grid, uint8_t *dst, int32_t dst_mem, int64_t dst_bytes,
@@ -277,8 +280,8 @@ VG_API void vg_batch_destroy(vg_batch *batch);
  * Host-only half of a step: validates the n frames and writes their
  * descriptors into the batch's pinned table, and applies the grids'
  * host-side state changes: a grid's pending re-centre is taken into this
- * step's merge, and a frame's own re-centre is left pending on its grid
- * (origin updated), as vg_shift leaves it.  Waits for the previous step's table copy, so the table can be
+ * step's merge, and a frame's own re-centre moves its grid's origin and
+ * ring and is left pending, as vg_shift leaves it.  Waits for the previous step's table copy, so the table can be
  * rewritten.  Grids must have vox_inf <= 3 and live on the batch's device.
  * Errors: VG_EINVAL (bad frame, two frames for one grid, n > capacity),
  * VG_ECUDA.
@@ -288,7 +291,8 @@ VG_API int vg_batch_prepare(vg_batch *batch, const vg_frame *frames, int32_t n);
 /*
  * Device half of a step: copies the table to the device and launches the
  * fused kernel on `stream` (cooperative launch: K1, K2, K3 and K4 of
- * every prepared frame, the merge applying each grid's pending re-centre,
+ * every prepared frame, each grid's merge clearing what a pending re-centre
+ * brought in,
  * with a grid-wide barrier between phases).  Can be captured in a CUDA graph; replaying the graph runs
  * whatever vg_batch_prepare wrote last.  Errors: VG_EINVAL, VG_ECUDA.
  */
@@ -313,8 +317,7 @@ VG_API int vg_batch_status(vg_batch *batch);
  *  VG_TUNE_BATCH_INFLATE_SLICES
  *                             slices of an inflate tile (phase 2): 8 (the
  *                             default; 0 selects it) or 4.
- *  VG_TUNE_BATCH_MERGE_WORDS  plane words per merge unit (phase 4) of a
- *                             grid whose merge applies a re-centre: 512 (the
+ *  VG_TUNE_BATCH_MERGE_WORDS  plane words per merge unit (phase 4): 512 (the
  *                             default; 0 selects it) or 256.
  *  VG_TUNE_BATCH_SPREAD       how phase 3 (the ray trace) shares its units,
  *                             groups of 256 / LPR rays, among the CTAs' contiguous
@@ -521,8 +524,8 @@ VG_API int vg_profile_read(vg_grid *grid, double ms[VG_NKERNELS], int64_t timed[
  *                    K3's CTAs per SM, 1 .. the occupancy limit (5), or 0
  *                    for the limit (default).
  *  VG_TUNE_MERGE_WORDS
- *                    plane words per CTA of K4 when it applies a pending
- *                    re-centre: 256 (default) or 512.
+ *                    plane words per CTA of K4: 256 (default, one per
+ *                    thread) or 512 (two per thread).
  *  VG_TUNE_INFLATE_TMA
  *                    1 (default): K2 moves each tile's raw words with one
  *                    tensor-memory-accelerator copy (radius 1..3); 0: its

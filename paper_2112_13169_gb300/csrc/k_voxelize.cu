@@ -6,10 +6,9 @@ namespace vg {
 namespace {
 
 // K1 lets the frame's later kernels launch only once the work before the
-// frame has completed (K4 stages the grid before it waits for K3): with
-// `early` right after its own wait, so that K2's launch overlaps K1;
-// without, when K1 completes, which leaves K1's SM slots to K3's CTAs,
-// whose walk runs before they wait for K2.
+// frame has completed: with `early` right after its own wait, so that K2's
+// launch overlaps K1; without, when K1 completes, which leaves K1's SM
+// slots to K3's CTAs, whose walk runs before they wait for K2.
 template <int DT, bool VEC>
 __global__ void __launch_bounds__(256) k_voxelize_depth(const FrameArgs a, const int early) {
     pdl_wait();   // the depth image and the planes belong to earlier work

@@ -29,10 +29,9 @@ namespace vg {
 // Every such kernel waits in every CTA before it ends, so its completion
 // implies its predecessor's, and by induction all earlier work's.  Without
 // a programmatic predecessor both are no-ops.  K1, the first kernel of a
-// frame, triggers only after its own wait: the frame's later kernels then
-// launch only once all work before the frame has completed, which lets K4
-// read the grid (written by the previous frame, not by K1-K3) before its
-// own wait.
+// frame, triggers only after its own wait (or not at all): the frame's
+// later kernels then launch only once all work before the frame has
+// completed.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
