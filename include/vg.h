@@ -9,7 +9,8 @@
  *   K2 inflate by vox_inf       (Sec. IV-B, Alg. 1, the three nested loops)
  *   K3 free-space ray-trace     (Sec. IV-C, Alg. 2)
  *   K4 merge into loc_grid      (Sec. IV-D, Alg. 3)
- *   K5 shift (re-centre)        (Sec. IV-E)
+ *   K5 shift (re-centre)        (Sec. IV-E; on the device a move of the
+ *                               grid's ring, which K4 and the reads follow)
  * There is no CPU fallback: every call either enqueues device work or fails.
  *
  * Conventions shared by all entry points
