@@ -170,7 +170,7 @@ def test_batch_applies_a_pending_shift(vg):
     batch.step(R.frames(1))
     assert batch.status() == vg.VG_OK
     R.oracle_step(1)
-    R.check("after the step")                       # the read applies the pending re-centre
+    R.check("after the step")                       # read out with the step's re-centre pending
     gb.shift(f2.robot_pos)
     og.shift(f2.robot_pos)
     batch.step(R.frames(2, recentre=False))

@@ -79,8 +79,9 @@ class Pair:
 def run_workload(vg, w, nframes, lanes=None, device=True, shift=True, flags=0):
     """Frames with a re-centre after each.  A grid is read (and compared)
     after every frame but not after its re-centre, so the re-centre is
-    still pending when the next frame comes and that frame's merge applies
-    it; the last re-centre is applied on its own by the final read."""
+    still pending when the next frame comes and that frame's merge clears
+    what it brought in; the last one is only read out (through the ring)
+    by the final read."""
     g = w.grid
     f0 = w.frames[0]
     P = Pair(vg, g.n, g.vox_size, w.cam.fov_x, w.cam.fov_y, g.depth, g.vox_inf, f0.robot_pos, lanes, flags=flags)
@@ -341,8 +342,9 @@ def test_axis_aligned_rays(vg):
 
 @pytest.mark.parametrize("read_after_shift", [True, False])
 def test_shifts(vg, read_after_shift):
-    # read_after_shift: each re-centre is applied on its own (K5) by the
-    # read; else the next frame's merge applies it
+    # read_after_shift: each re-centre is read out through the ring (K5)
+    # while pending; else only after the next frame's merge has cleared
+    # what it brought in
     rng = np.random.default_rng(13)
     P = _pair(vg, n=(30, 20, 10), pos=(0.0, 0.0, 0.0))
     P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([0, 0, 0]))
@@ -379,7 +381,8 @@ def test_reads_of_a_pending_shift_leave_the_grid_alone(vg):
     # a read with a re-centre pending writes the re-centred grid into dst:
     # straight into device memory or page-locked host memory (aligned), or
     # through the second buffer (unaligned device memory, pageable memory);
-    # none of them applies the re-centre, which the next merge still does
+    # none of them changes the grid, whose next merge still clears what the
+    # re-centre brought in
     rng = np.random.default_rng(16)
     P = _pair(vg, n=(45, 31, 10))
     P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose([0.1, 0.2, 0.3], 0.2))
