@@ -3,7 +3,8 @@
 
 A step is one measurement of the plain per-frame path: K1 voxelize, K2
 inflate, K3 ray-trace, K4 merge (vg_integrate_depth) and the re-centre
-(vg_shift, applied by the next frame's K4), on the default workload
+(vg_shift: a move of the grid's ring, whose new voxels the next frame's K4
+sets to unknown), on the default workload
 "seq": 640x480 float32 depth frames
 along a seeded trajectory through a 20x20x5 m scene of 200 boxes and
 cylinders, depth 5 m, 10% invalid pixels, depth noise sigma 1% of depth,
@@ -253,7 +254,10 @@ def algorithmic_bytes(kind, w):
       K2 inflate   occ_raw read + occ_inf written      2N/8
       K3 raytrace  occ_inf read + free, traced written 3N/8
       K4 merge     loc read + written, 3 planes read   2N + 3N/8
-      K5 shift     loc read + written                  2N"""
+      K5 shift     loc read + written                  2N
+    (K4 counts the merge with the re-centre's copy of loc, as the workload's
+    model does; the ring-addressed grid writes only the voxels a frame marks
+    and moves less.)"""
     n = w.nvox
     px = w.cam.W * w.cam.H * (2 if w.cam.dtype == "u16" else 4)
     return {"voxelize": px + n / 8, "inflate": 2 * n / 8, "raytrace": 3 * n / 8,
@@ -261,7 +265,7 @@ def algorithmic_bytes(kind, w):
 
 
 def frame_bytes(w):
-    """Algorithmic bytes of one frame (K1..K4, the re-centre inside K4)."""
+    """Algorithmic bytes of one frame (K1..K4, the re-centre counted in K4)."""
     return sum(algorithmic_bytes(k, w) for k in ("voxelize", "inflate", "raytrace", "merge"))
 
 
@@ -437,7 +441,7 @@ def measure_batched(vg, args, dist, stream):
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     lat = [a.elapsed_time(b) for a, b in ev]
-    out["plain"] = {"form": "plain: one launch per kernel (K1-K4, the re-centre inside K4), robot after robot",
+    out["plain"] = {"form": "plain: one launch per kernel (K1-K4, the re-centre a ring move), robot after robot",
                     "steps": psteps, "value": agg(nvox * psteps, sum(lat) / 1e3), "unit": "Mvoxel-updates/s",
                     "step_ms": _pcts(lat)}
     for g in gp:
