@@ -528,6 +528,30 @@ def test_read_write_roundtrip_and_resume(vg):
     P.close()
 
 
+def test_write_after_recentres(vg):
+    # re-centres move the grid's ring; a write replaces the grid whole (in
+    # its own frame), and frames and re-centres after it go on from there
+    rng = np.random.default_rng(47)
+    P = _pair(vg, n=(36, 28, 12))
+    pos = np.array([0.01, 0.02, 0.03])
+    for k in range(3):
+        P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose(pos, 0.5 * k))
+        pos = pos + np.array([0.23, -0.31, 0.12])
+        P.shift(pos, check=False)
+    prior = rng.integers(0, 4, size=P.g.shape).astype(np.uint8)
+    origin = np.array([5, -7, 2], np.int32)
+    P.g.write(torch.from_numpy(prior.ravel().copy()).cuda(), origin)
+    P.o.loc = prior.copy()
+    P.o.o = origin.copy()
+    P.check("after write")
+    pos = (origin + np.array([18, 14, 6])) * 0.1 + 0.01
+    for k in range(2):
+        P.depth(rng.uniform(0.2, 3.0, size=(24, 32)).astype(np.float32), body_pose(pos, -0.4 * k))
+        pos = pos + np.array([-0.17, 0.26, -0.05])
+        P.shift(pos)
+    P.close()
+
+
 def test_stats_count_points_and_visits(vg, orc):
     from oracle import OracleParams as OP
     rng = np.random.default_rng(23)
