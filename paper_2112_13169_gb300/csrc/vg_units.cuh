@@ -459,20 +459,28 @@ __device__ __forceinline__ void shift_chunk(const PlaneGeom &g, const Ring &R, c
 #pragma unroll
         for (int m = 0; m < 4; ++m) o[m] = __funnelshift_r(wv[m], wv[m + 1], sh);
     } else {
+        // byte by byte, through at most two rows: each row's ring position
+        // and whether a re-centre brought it in are found once, and the
+        // buffer x advances with the voxel (wrapping at the row's end)
         uint8_t ob[16];
+        const uint8_t *rowp =
+            src + ((int64_t)ring_at(z, R.r[2], g.nz) * g.ny + ring_at(y, R.r[1], g.ny)) * g.nx;
+        bool rin = row_in;
+        int32_t xr = xb;
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
             ob[b] = 0;
-            if (i0 + b < g.nvox) {
-                const bool in = !((x >= R.elo[0] && x < R.ehi[0]) || (y >= R.elo[1] && y < R.ehi[1]) ||
-                                  (z >= R.elo[2] && z < R.ehi[2]));
-                if (in)
-                    ob[b] = L::ld(src + ((int64_t)ring_at(z, R.r[2], g.nz) * g.ny + ring_at(y, R.r[1], g.ny)) * g.nx +
-                                  ring_at(x, R.r[0], g.nx));
-            }
+            if (i0 + b < g.nvox && rin && !(x >= R.elo[0] && x < R.ehi[0])) ob[b] = L::ld(rowp + xr);
             if (++x == g.nx) {
                 x = 0;
                 if (++y == g.ny) { y = 0; ++z; }
+                // the next row (past the grid's end only where no voxel is read)
+                const int32_t zr = z < g.nz ? z : 0;
+                rowp = src + ((int64_t)ring_at(zr, R.r[2], g.nz) * g.ny + ring_at(y, R.r[1], g.ny)) * g.nx;
+                rin = !((y >= R.elo[1] && y < R.ehi[1]) || (z >= R.elo[2] && z < R.ehi[2]));
+                xr = R.r[0];
+            } else if (++xr == g.nx) {
+                xr = 0;
             }
         }
 #pragma unroll
