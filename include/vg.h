@@ -322,12 +322,13 @@ VG_API int vg_batch_status(vg_batch *batch);
  *                             default; 0 selects it) or 256.
  *  VG_TUNE_BATCH_SPREAD       how phase 3 (the ray trace) shares its units,
  *                             groups of 256 / LPR rays, among the CTAs' contiguous
- *                             runs.  2 (default): one unit per group; the runs
- *                             split the units' total estimated cost evenly
- *                             (each frame's unit cost from 25 of its rays'
- *                             lengths in the grid).  1: each frame's rays are
+ *                             runs.  1 (default): each frame's rays are
  *                             spread over proportionally more units, so that
- *                             the runs hold equal numbers of units.  0: one
+ *                             the runs hold equal numbers of units.  2: one
+ *                             unit per group; the runs split the units' total
+ *                             estimated cost evenly (each frame's unit cost
+ *                             from 25 of its rays' lengths in the grid), which
+ *                             suits batches of frames of unlike cost.  0: one
  *                             unit per group, equal numbers of units.
  *  VG_TUNE_BATCH_BARRIER_US   how long a CTA of the fused launch waits at a
  *                             grid barrier before it gives up, in

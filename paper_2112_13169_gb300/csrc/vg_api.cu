@@ -757,7 +757,7 @@ int vg_batch_create(int32_t capacity, vg_batch **out) {
     B->capacity = capacity;
     B->inflate_tz = 8;
     B->merge_words = vg::kBatchMergeWords;
-    B->spread = 2;
+    B->spread = 1;
     B->bar_ns = vg::kBarrierNs;
     B->bytes = sizeof(vg::BatchCtl) + (size_t)capacity * sizeof(vg::BatchItem);
     cudaError_t e = cudaGetDevice(&B->device);
